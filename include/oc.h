@@ -1,0 +1,246 @@
+/*
+ * oc.h -- C ABI of the out-of-core stencil loop-chain executor (liboc.so).
+ *
+ * Method: "Beyond 16GB: Out-of-Core Stencil Computations" (arXiv 1709.02125).
+ *   - Sec. 3: the OPS abstraction -- datasets on a structured block, stencils
+ *     (sets of relative offsets), and parallel loops over an iteration range
+ *     whose arguments carry an access mode (read / write / read-write). Points of
+ *     a loop may run in any order. Loops are queued lazily; any call that returns
+ *     data to the user ends the chain and forces execution, and a dependency
+ *     analysis turns the chain into a skewed tiling along one axis.
+ *   - Sec. 4, Algorithm 1: tiles are streamed through a bounded device memory
+ *     with three CUDA streams (upload / compute / download).
+ *   - Sec. 4.1: read-only data is never downloaded, write-first data is never
+ *     uploaded, the unsafe "cyclic" option skips downloads of write-first data,
+ *     and the first tile of the next chain is prefetched speculatively.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns OC_OK (0) or a negative OC_ERR_* code; the message of
+ *     the last failure is returned by oc_last_error(). No entry point aborts the
+ *     process on bad input.
+ *   - One context per process, created by oc_init() and destroyed by
+ *     oc_finalize(). The library is not thread-safe: call it from one host thread.
+ *   - Handles (datasets, reductions) are small non-negative ints.
+ *   - Coordinates: x is the fastest axis. The slowest axis (y in 2-D, z in 3-D) is
+ *     the tiling axis. Interior indices run 0..n-1; halo indices are negative or
+ *     >= n. A point p of a loop range is (x, y[, z]).
+ *   - Host arrays handed to / returned by the library are dense C-order arrays of
+ *     the full allocated extent INCLUDING halos: for a 2-D dataset of size
+ *     (nx, ny) with halos (hlo, hhi) the array has shape
+ *     (ny + hlo[1] + hhi[1], nx + hlo[0] + hhi[0]) and element (x, y) lives at
+ *     [(y + hlo[1]) * (nx + hlo[0] + hhi[0]) + (x + hlo[0])]; 3-D likewise with z
+ *     outermost.
+ */
+#ifndef OC_H
+#define OC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define OC_OK            0
+#define OC_ERR_ARG      -1  /* invalid argument, handle, range or stencil          */
+#define OC_ERR_BUDGET   -2  /* the device budget cannot hold one tile of the chain  */
+#define OC_ERR_CUDA     -3  /* a CUDA runtime call failed (message has the reason)  */
+#define OC_ERR_TIMEOUT  -4  /* a bounded wait on a stream or event expired          */
+#define OC_ERR_STATE    -5  /* call out of order (no context, double init, ...)     */
+#define OC_ERR_NOMEM    -6  /* host (pinned) allocation failed                      */
+
+/* ---- element types ------------------------------------------------------- */
+#define OC_F64 0
+#define OC_F32 1
+
+/* ---- access modes (Sec. 3: read / write / both; plus reductions) --------- */
+#define OC_READ   1
+#define OC_WRITE  2
+#define OC_RW     3
+#define OC_REDUCE 4   /* oc_arg.dat is a reduction handle, not a dataset */
+
+/* ---- reduction operators ---------------------------------------------------- */
+#define OC_SUM 0
+#define OC_MAX 1
+#define OC_MIN 2
+
+/* ---- context flags (oc_init / oc_set_flag) ----------------------------------
+ * OC_FLAG_CYCLIC   Sec. 4.1 "cyclic" optimisation: datasets whose first access in a
+ *                  chain is a write are treated as per-chain temporaries and are
+ *                  never downloaded. UNSAFE if such a dataset is read by a later
+ *                  chain or fetched: its host copy is then stale. Off by default.
+ * OC_FLAG_PREFETCH Sec. 4.1 speculative prefetch: while the last tile of a chain
+ *                  runs, upload the first tile of the next chain assuming it has
+ *                  the same plan; the next chain uploads only what is missing.
+ * OC_FLAG_GRAPHS   capture the kernels of each tile once as a CUDA graph and replay
+ *                  it when the same chain shape runs again.
+ * OC_FLAG_DRYRUN   no device at all: chains are analysed and planned (the plan can
+ *                  be inspected with oc_plan_*), nothing is executed, and
+ *                  oc_reduce / oc_fetch_dat return OC_ERR_STATE. Host-only use.   */
+#define OC_FLAG_CYCLIC   0x1u
+#define OC_FLAG_PREFETCH 0x2u
+#define OC_FLAG_GRAPHS   0x4u
+#define OC_FLAG_DRYRUN   0x8u
+
+/* ---- planner modes ----------------------------------------------------------
+ * OC_PLAN_FIXED     largest tile height whose plan fits the budget, depth 3.
+ * OC_PLAN_AUTOTUNE  time every (tile height, depth) candidate of the grid on the
+ *                   first execution of a chain shape and keep the fastest.
+ * OC_PLAN_LEARNED   MLP prediction from chain features (oc_planner_load), snapped
+ *                   to the grid; falls back to AUTOTUNE when no network is loaded. */
+#define OC_PLAN_FIXED    0
+#define OC_PLAN_AUTOTUNE 1
+#define OC_PLAN_LEARNED  2
+
+/* ---- loop kernels (kernel_id of oc_enqueue_loop) ------------------------------
+ * Every kernel is a pointwise function of its READ arguments sampled at their
+ * stencil offsets; WRITE/RW arguments are accessed at offset 0 only. For every
+ * point the result is evaluated in exactly the order written below (IEEE
+ * round-to-nearest, no fused multiply-add), so that any two correct
+ * implementations agree bit for bit on FP64 data.
+ *
+ * OC_K_COPY     args: [0] WRITE dst (1 point, offset 0), [1] READ src (1 point).
+ *               dst(p) = src(p + o).                               params: none.
+ * OC_K_LINCOMB  args: [0] WRITE dst; [1..k] READ inputs, input j with n_j points.
+ *               Let x_0..x_{M-1} be the samples in argument order, then point
+ *               order (M = sum n_j). params = [alpha, c_0, ..., c_{M-1}].
+ *               acc = c_0*x_0; acc = acc + c_m*x_m for m = 1..M-1; if alpha != 0:
+ *               acc = acc + ((alpha*a)*b) / (1 + c*c) with a = x_0,
+ *               b = x_{1 mod M}, c = x_{2 mod M}. dst(p) = acc.
+ * OC_K_REDUCE   args: [0] READ src0 (offset 0), optionally [1] READ src1 (offset 0),
+ *               last: REDUCE handle. v = src0(p) (+ src1(p)), converted to double
+ *               before the addition; params = [mode]: 0 -> v, 1 -> |v|, 2 -> v*v.
+ *               The handle's operator folds v over the range (see oc_reduce).
+ * OC_K_HILO_ADD args: [0] RW hi (F32), [1] RW lo (F32), [2] READ du (offset 0).
+ *               params = [scale]. Compensated update of the pair value hi+lo by
+ *               y = (float)scale * du, all in FP32: s = hi + y; z = s - hi;
+ *               e = (hi - (s - z)) + (y - z); l = lo + e; hi' = s + l;
+ *               lo' = l - (hi' - s).   (TwoSum followed by Fast2Sum.)
+ * The Euler (OC_K_EULER_*) and Navier-Stokes (OC_K_NS_*) kernels are declared in
+ * oc_physics.h.
+ */
+#define OC_K_COPY     1
+#define OC_K_LINCOMB  2
+#define OC_K_REDUCE   3
+#define OC_K_HILO_ADD 4
+
+/* One loop argument (Sec. 3: dataset + stencil + access mode). For OC_REDUCE,
+ * `dat` is a reduction handle and npoints/offsets are ignored. `offsets` holds
+ * npoints * ndim ints (x, y[, z] per point); it is copied at enqueue time. */
+typedef struct oc_arg {
+    int dat;
+    int access;
+    int npoints;
+    const int* offsets;
+} oc_arg;
+
+/* Counters of the last flush and running totals (all chains since oc_init). */
+typedef struct oc_stats_t {
+    double seconds;        /* host wall time of the last flush, copies included      */
+    double cell_updates;   /* sum over executed loops of their range points          */
+    double hbm_bytes;      /* algorithmic bytes (Sec. 5.1: 1x read or write, 2x RW)  */
+    double h2d_bytes;      /* bytes uploaded host -> device in the last flush        */
+    double d2h_bytes;      /* bytes downloaded device -> host in the last flush      */
+    double prefetched_bytes; /* bytes of the last flush's uploads already prefetched */
+    int    tiles;          /* tiles of the last flush (1 = in-core)                  */
+    int    tile_height;    /* slow-axis rows per tile chosen by the planner          */
+    int    depth;          /* pipeline depth used (2..4)                             */
+    int    loops;          /* loops in the last chain                                */
+    int    graph_replays;  /* tiles of the last flush replayed from a CUDA graph     */
+    int    kernel_launches;/* kernels the last flush launched (graph nodes included) */
+    double total_seconds, total_cell_updates, total_hbm_bytes, total_h2d_bytes,
+           total_d2h_bytes;
+    long long chains;
+} oc_stats_t;
+
+/* Create the context. Sec. 4: all tiles live inside a device budget.
+ *  device_budget_bytes  bytes of device memory the executor may use for dataset
+ *                       slabs and reduction scratch (the "fast memory" size).
+ *  device_arena         caller-owned device allocation of arena_bytes >= budget
+ *                       (e.g. a torch uint8 tensor); the library never frees it.
+ *                       NULL with arena_bytes == 0: the library allocates the
+ *                       budget itself and frees it in oc_finalize.
+ *  streams              three cudaStream_t handles (upload, compute, download) owned
+ *                       by the caller, or NULL: the library creates its own.
+ *  flags                OC_FLAG_* bits.  planner_mode: OC_PLAN_*.
+ * Errors: OC_ERR_STATE if a context exists; OC_ERR_ARG on an arena smaller than
+ * the budget; OC_ERR_CUDA if the device cannot be used (not with OC_FLAG_DRYRUN). */
+int oc_init(size_t device_budget_bytes, void* device_arena, size_t arena_bytes,
+            void* const streams[3], uint32_t flags, int planner_mode);
+
+/* Flush nothing, release every resource (pinned host stores, graphs, events,
+ * library-owned streams and arena). Pending chains are discarded. */
+int oc_finalize(void);
+
+/* Declare a dataset (Sec. 3 "datasets"; data is handed to the library, Sec. 3).
+ *  ndim 2 or 3; size = interior extent; halo_lo/halo_hi = halo depth per axis.
+ *  dtype OC_F64 or OC_F32. host_init: dense array of the full extent (see top)
+ *  copied into a library-owned pinned host store, or NULL for zeros.
+ *  periodic_mask bit a: axis a is periodic. A periodic non-slow axis must have zero
+ *  halo (kernels that support it wrap indices); a periodic slow axis has its halo
+ *  layers refreshed from the opposite end at the start of every chain ("deep
+ *  ghosts"), so loops may iterate into them.  *dat_out receives the handle. */
+int oc_decl_dat(int ndim, const int size[3], const int halo_lo[3], const int halo_hi[3],
+                int dtype, const void* host_init, int periodic_mask, int* dat_out);
+
+/* Declare a reduction handle with operator OC_SUM / OC_MAX / OC_MIN. Its value is
+ * folded over every loop of a chain that names it; a chain that names it again
+ * after its value was read starts from the operator's identity. */
+int oc_decl_reduction(int op, int* red_out);
+
+/* Queue a loop (Sec. 3 parallel loop; lazy, nothing executes). range_lo/range_hi:
+ * half-open iteration range per axis (ndim taken from the first dataset argument).
+ * Validated now: dataset handles, access modes, a WRITE/RW argument must use exactly
+ * the single offset 0, a dataset written by the loop may not also be read at a
+ * non-zero offset, and every access must stay inside the allocated extent
+ * (non-slow periodic axes excepted). Errors: OC_ERR_ARG. */
+int oc_enqueue_loop(int kernel_id, const int range_lo[3], const int range_hi[3],
+                    int nargs, const oc_arg* args, const double* params, int nparams);
+
+/* Execute the queued chain (Sec. 3: a call returning data ends the chain; Sec. 4
+ * Algorithm 1 streams its tiles). Returns when every result is in host memory. */
+int oc_flush(void);
+
+/* Flush, then return the value of reduction `red` of the last chain that named it. */
+int oc_reduce(int red, double* out);
+
+/* Flush, then copy dataset `dat` (full extent, dense, see top) into host_out. */
+int oc_fetch_dat(int dat, void* host_out);
+
+/* Switch a OC_FLAG_CYCLIC / PREFETCH / GRAPHS bit on or off between chains (Sec. 4.1:
+ * the cyclic flag is set by the user once the cyclic phase of the run begins). */
+int oc_set_flag(uint32_t flag, int on);
+
+/* Override the planner: tile height in slow-axis rows (0 = planner decides) and
+ * pipeline depth 2..4 (0 = planner decides). Depth d uploads tile t+d-2 while tile t
+ * computes and tile t-1 downloads. */
+int oc_set_tiling(int tile_height, int depth);
+
+/* Copy the counters into *out. */
+int oc_stats(oc_stats_t* out);
+
+/* Message of the last error (static storage, valid until the next call). */
+const char* oc_last_error(void);
+
+/* ---- plan inspection (Sec. 3 skewed tiling, Sec. 4 footprints) -----------------
+ * Describe the plan of the most recent flush (also in OC_FLAG_DRYRUN mode).
+ * oc_plan_shape: number of tiles, loops, datasets used by the chain, tile height,
+ *   depth, and the number of slow-axis rows spanned by the loop ranges.
+ * oc_plan_ranges: se[(t*nloops + i)*2 + {0,1}] = half-open slow-axis range [s, e)
+ *   of loop i in tile t (s == e: loop i does nothing in tile t).
+ * oc_plan_dat: k-th dataset of the chain (0 <= k < ndats): its handle, slab rows S
+ *   (rows are stored at slot (y - y_first) mod S; S = all rows when in-core), and
+ *   the row intervals copied per tile: up[3*j] = tile, up[3*j+1..2] = [a, b) for
+ *   j < *nup (likewise down). Capacities in cap_up / cap_down triples; if too small
+ *   OC_ERR_ARG is returned and *nup / *ndown hold the required counts. */
+int oc_plan_shape(int* ntiles, int* nloops, int* ndats, int* tile_height, int* depth,
+                  int* slow_rows);
+int oc_plan_ranges(int* se);
+int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
+                int* down, int cap_down, int* ndown);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OC_H */
