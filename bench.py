@@ -1,0 +1,371 @@
+"""Benchmark of the out-of-core stencil loop-chain executor (arXiv 1709.02125).
+
+Workload: the synthetic random 2-D loop chain -- 24 FP64 fields of 4096^2 (halo 2),
+40 LINCOMB loops reading 1-4 fields at offsets within radius 2, plus 2 SUM reductions
+that the user reads after every chain -- executed with a device budget of 1/3 of the
+3.2 GB footprint (3x oversubscribed). One step = one chain (one oc_flush plus the two
+oc_reduce reads). Metric: cell-updates/s = sum over the loops of their range points,
+divided by the step time.
+
+Variants on fresh contexts: the headline mixed+learned form (fields stored and
+computed in FP32, sums in FP64, learned tile planner, prefetch and CUDA graphs), the
+FP64 plain out-of-core form, and FP64 in-core (budget above the footprint).
+
+`--impl reference` times the oracle (plain untiled FP64 C, OpenMP on the host cores)
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "out-of-core cell-updates/s at 3x mem: mixed+learned tiling vs FP64 plain"
+UNIT = "cell-updates/s"
+WORKLOAD = ("random 2-D loop chain: 24 fields x 4096^2 (halo 2), 40 LINCOMB loops (1-4 inputs, "
+            "radius-2 offsets) + 2 SUM reductions per chain, device budget 1/3 of the footprint")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def link_bandwidth(torch, nbytes=1 << 30):
+    """Pinned host <-> device copy GB/s (H2D, D2H, both directions at once)."""
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = {}
+    for name in ("h2d", "d2h", "duplex"):
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name in ("h2d", "duplex"):
+                with torch.cuda.stream(s1):
+                    d.copy_(h, non_blocking=True)
+            if name in ("d2h", "duplex"):
+                with torch.cuda.stream(s2):
+                    h2.copy_(d2, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = max(best, (2 if name == "duplex" else 1) * nbytes / dt / 1e9)
+        out[f"{name}_gbs"] = round(best, 1)
+    del h, h2, d, d2
+    return out
+
+
+def build_workload(dtype: str, n: int):
+    from workloads import random_chain
+    dats, reds, loops = random_chain.build(n=n, dtype=dtype)
+    if dtype == "f32":
+        for d in dats:
+            d.init = d.init.astype(np.float32)
+    fp = random_chain.footprint_bytes(n, 24, 8 if dtype == "f64" else 4)
+    return dats, reds, loops, fp
+
+
+def run_variant(torch, name, dtype, budget_frac, flags, planner, steps, warmup, n, dist, profile_kernel=None):
+    from paper_1709_02125_gb300 import oc
+    dats, reds, loops, fp = build_workload(dtype, n)
+    budget = int(fp * budget_frac)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    ex = oc.Executor(budget, flags=flags, planner=planner, arena=arena, streams=streams)
+    try:
+        for d in dats:
+            ex.decl_dat(d)
+            d.init = None  # the library holds its own pinned copy
+        for r in reds:
+            ex.decl_reduction(r.name, r.op)
+
+        def step():
+            for lp in loops:
+                ex.enqueue(lp)
+            ex.flush()
+            return [ex.reduce(r.name) for r in reds]
+
+        for _ in range(warmup):
+            step()
+        if profile_kernel:
+            ex.set_flag(oc.OC_FLAG_PROFILE, True)
+            ex.kernel_stats_reset()
+        s0 = ex.stats()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(streams[1])
+        t0 = time.perf_counter()
+        launches = 0
+        vals = None
+        for _ in range(steps):
+            vals = step()
+            launches += ex.stats()["kernel_launches"]
+        e1.record(streams[2])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        dev_s = e0.elapsed_time(e1) / 1e3
+        if dist:
+            t = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dev_s, wall = float(t[0]), float(t[1])
+        s1 = ex.stats()
+        res = {
+            "dtype": dtype, "budget_bytes": budget, "footprint_bytes": fp,
+            "cells_per_step": (s1["total_cell_updates"] - s0["total_cell_updates"]) / steps,
+            "hbm_bytes_per_step": (s1["total_hbm_bytes"] - s0["total_hbm_bytes"]) / steps,
+            "h2d_bytes_per_step": (s1["total_h2d_bytes"] - s0["total_h2d_bytes"]) / steps,
+            "d2h_bytes_per_step": (s1["total_d2h_bytes"] - s0["total_d2h_bytes"]) / steps,
+            "device_s": dev_s, "wall_s": wall, "tiles": s1["tiles"], "tile_height": s1["tile_height"],
+            "depth": s1["depth"], "kernel_launches": launches, "graph_replays": s1["graph_replays"],
+            "prefetched_bytes": s1["prefetched_bytes"], "sums": vals,
+        }
+        if profile_kernel:
+            res["kstats"] = ex.kernel_stats(profile_kernel)
+        return res
+    finally:
+        ex.close()
+        del arena
+
+
+def reference_main(args):
+    """Time the oracle (plain untiled FP64 C with OpenMP) on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from workloads import random_chain
+    oracle.build()
+    n = args.n
+    dats, reds, loops = random_chain.build(n=n)
+    fields = oracle.make_fields(dats)
+    # bound the sample: rows of the slow axis processed per step
+    t0 = time.perf_counter()
+    oracle.run_chain(loops, fields, reds)
+    one = time.perf_counter() - t0
+    rows = n
+    if one * (args.steps + args.warmup) > args.ref_budget_s:
+        rows = max(64, int(n * args.ref_budget_s / (one * (args.steps + args.warmup + 1))))
+    sub = [type(lp)(lp.kernel, lp.lo, (lp.hi[0], min(lp.hi[1], rows)), lp.args, lp.params) for lp in loops]
+    for _ in range(args.warmup):
+        oracle.run_chain(sub, fields, reds)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run_chain(sub, fields, reds)
+    dt = time.perf_counter() - t0
+    cells = sum(np.prod([h - l for l, h in zip(lp.lo, lp.hi)]) for lp in sub) * args.steps
+    v = float(cells / dt)
+    cores = oracle.threads()
+    sample = f"full chain (42 loops) on {n} x {rows} rows of the {n}^2 grid per step" if rows < n else \
+        f"full chain (42 loops) on the full {n}^2 grid per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_rows_per_step": rows},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(n, budget_s=20.0):
+    import oracle
+    from workloads import random_chain
+    oracle.build()
+    dats, reds, loops = random_chain.build(n=n)
+    fields = oracle.make_fields(dats)
+    t0 = time.perf_counter()
+    chains = 0
+    cells = 0
+    while time.perf_counter() - t0 < budget_s and chains < 8:
+        oracle.run_chain(loops, fields, reds)
+        chains += 1
+        cells += sum(np.prod([h - l for l, h in zip(lp.lo, lp.hi)]) for lp in loops)
+    dt = time.perf_counter() - t0
+    return {"value": float(cells / dt), "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{chains} full chains (42 loops, {n}^2 grid, FP64) in {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--ref-budget-s", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    import __graft_entry__
+    from paper_1709_02125_gb300 import oc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    oc.load()
+
+    link = link_bandwidth(torch)
+    variants = {
+        "mixed_learned": ("f32", 1 / 3, oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS, oc.OC_PLAN_LEARNED),
+        "fp64_plain": ("f64", 1 / 3, 0, oc.OC_PLAN_FIXED),
+        "fp64_opt": ("f64", 1 / 3, oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS, oc.OC_PLAN_FIXED),
+        "fp64_incore": ("f64", 1.25, oc.OC_FLAG_GRAPHS, oc.OC_PLAN_FIXED),
+    }
+    results = {}
+    clk = None
+    for name in args.variants.split(","):
+        dtype, frac, flags, planner = variants[name]
+        if name == "mixed_learned":
+            with Clocks(local) as clk:
+                results[name] = run_variant(torch, name, dtype, frac, flags, planner, args.steps, args.warmup,
+                                            args.n, dist, profile_kernel="lincomb")
+        else:
+            results[name] = run_variant(torch, name, dtype, frac, flags, planner, args.steps, args.warmup,
+                                        args.n, dist)
+    head = results.get("mixed_learned") or next(iter(results.values()))
+    N = world
+    value = N * head["cells_per_step"] * args.steps / head["device_s"]
+    e2e_value = N * head["cells_per_step"] * args.steps / head["wall_s"]
+    hbm_peak, peak_kind = _peaks()
+    ks = head.get("kstats") or {}
+    roof = None
+    if ks.get("ms"):
+        achieved = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_lincomb<float>", "achieved": round(achieved, 1),
+                "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": None, "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
+                "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"]}
+    # binding roofline of the whole pipeline: HBM bytes at peak, link bytes at the link speed
+    t_step = head["device_s"] / args.steps
+    t_roof = max(head["hbm_bytes_per_step"] / (hbm_peak * 1e9), head["h2d_bytes_per_step"] / (link["h2d_gbs"] * 1e9),
+                 head["d2h_bytes_per_step"] / (link["d2h_gbs"] * 1e9),
+                 (head["h2d_bytes_per_step"] + head["d2h_bytes_per_step"]) / (link["duplex_gbs"] * 1e9))
+    variants_out = {}
+    for k, r in results.items():
+        v = N * r["cells_per_step"] * args.steps / r["device_s"]
+        variants_out[k] = {"value": v, "dtype": r["dtype"], "ms_per_step": r["device_s"] / args.steps * 1e3,
+                           "tiles": r["tiles"], "tile_height": r["tile_height"], "depth": r["depth"],
+                           "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
+                           "budget_bytes": r["budget_bytes"]}
+    if "fp64_plain" in variants_out and "fp64_incore" in variants_out:
+        variants_out["fp64_plain"]["frac_of_incore"] = variants_out["fp64_plain"]["value"] / variants_out["fp64_incore"]["value"]
+    if "mixed_learned" in variants_out and "fp64_plain" in variants_out:
+        variants_out["mixed_learned"]["speedup_vs_fp64_plain"] = (variants_out["mixed_learned"]["value"]
+                                                                 / variants_out["fp64_plain"]["value"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["device_s"] / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": head["dtype"] + "+f64-reductions", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": "mixed_learned" if "mixed_learned" in results else args.variants,
+                   "budget_bytes": head["budget_bytes"], "footprint_bytes": head["footprint_bytes"],
+                   "tiles": head["tiles"], "tile_height": head["tile_height"], "depth": head["depth"],
+                   "l2": "inputs 3.2 GB (1.6 GB FP32) > 129 MB L2: no flush needed",
+                   "parallelism": f"replicas x{N}"},
+        "roofline": roof,
+        "pipeline_roofline": {"t_roof_ms": t_roof * 1e3, "t_ms": t_step * 1e3, "frac": t_roof / t_step,
+                              "link": link, "hbm_peak_gbs": hbm_peak},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": head["d2h_bytes_per_step"] + 16},
+        "gpu_launches": int(head["kernel_launches"]),
+        "clocks": clk.summary() if clk else None,
+        "variants": variants_out,
+    }
+    if rank == 0 and N == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

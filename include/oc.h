@@ -77,11 +77,14 @@ extern "C" {
  *                  it when the same chain shape runs again.
  * OC_FLAG_DRYRUN   no device at all: chains are analysed and planned (the plan can
  *                  be inspected with oc_plan_*), nothing is executed, and
- *                  oc_reduce / oc_fetch_dat return OC_ERR_STATE. Host-only use.   */
+ *                  oc_reduce / oc_fetch_dat return OC_ERR_STATE. Host-only use.
+ * OC_FLAG_PROFILE  bracket every kernel launch with CUDA events on the compute
+ *                  stream and accumulate per-kernel device time (oc_kernel_stats). */
 #define OC_FLAG_CYCLIC   0x1u
 #define OC_FLAG_PREFETCH 0x2u
 #define OC_FLAG_GRAPHS   0x4u
 #define OC_FLAG_DRYRUN   0x8u
+#define OC_FLAG_PROFILE  0x10u
 
 /* ---- planner modes ----------------------------------------------------------
  * OC_PLAN_FIXED     largest tile height whose plan fits the budget, depth 3.
@@ -219,6 +222,18 @@ int oc_set_tiling(int tile_height, int depth);
 
 /* Copy the counters into *out. */
 int oc_stats(oc_stats_t* out);
+
+/* Per-kernel device time measured with OC_FLAG_PROFILE (accumulated until reset).
+ * bytes = algorithmic bytes of the launches (Sec. 5.1 formula: every dataset argument
+ * moves its range once, twice if read-write), points = range points. */
+typedef struct oc_kernel_stats_t {
+    long long launches;
+    double ms;
+    double bytes;
+    double points;
+} oc_kernel_stats_t;
+int oc_kernel_stats(int kernel_id, oc_kernel_stats_t* out);
+int oc_kernel_stats_reset(void);
 
 /* Message of the last error (static storage, valid until the next call). */
 const char* oc_last_error(void);

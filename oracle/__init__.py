@@ -83,6 +83,7 @@ class Field:
         self.geo = np.array(ext + hl, dtype=np.int32)
 
     def check(self, lo, hi, offs):
+        offs = [tuple(o) + (0,) * (3 - len(o)) for o in offs]
         for a in range(self.ndim):
             omin = min(o[a] for o in offs)
             omax = max(o[a] for o in offs)
@@ -98,7 +99,7 @@ def _r3(lo, hi, nd):
 
 
 def _o3(offs, nd):
-    return [tuple(o) + (0,) * (3 - nd) for o in offs]
+    return [tuple(o) + (0,) * (3 - len(o)) for o in offs]
 
 
 def run_loop(loop, fields: Dict[str, Field], reds: Dict[str, float], red_ops: Dict[str, str]):

@@ -1,0 +1,69 @@
+"""Build liboc.so in-tree with nvcc for sm_103a (GB300).
+
+Every translation unit is compiled separately (in parallel) and linked into
+`paper_1709_02125_gb300/_lib/liboc.so`. Flags: -fmad=false keeps every floating-point
+operation separately rounded (the evaluation order of include/oc.h is then exact),
+-lineinfo keeps source lines for profilers.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+OUT_DIR = os.path.join(HERE, "_lib")
+SO = os.path.join(OUT_DIR, "liboc.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+SOURCES = ["runtime.cu", "analysis.cpp", "planner.cpp", "physics_host.cpp",
+           "kernels_core.cu", "kernels_physics.cu"]
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+
+
+def _flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+                   "-Xcompiler", "-ffp-contract=off", f"-I{os.path.join(ROOT, 'include')}"]
+
+
+def _deps_newer(target: str) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", f)
+                                                                 for f in os.listdir(os.path.join(ROOT, "include"))]
+    return any(os.path.getmtime(f) > t for f in files)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link liboc.so; returns its path. Skips work if it is up to date."""
+    if not force and not _deps_newer(SO):
+        return SO
+    os.makedirs(os.path.join(OUT_DIR, "obj"), exist_ok=True)
+
+    def compile_one(src):
+        obj = os.path.join(OUT_DIR, "obj", src + ".o")
+        cmd = [NVCC] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+        if src.endswith(".cpp"):
+            cmd = [NVCC, "-x", "cu"] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = SO + f".tmp{os.getpid()}"
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, SO)
+    return SO
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

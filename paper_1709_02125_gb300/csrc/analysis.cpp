@@ -1,0 +1,332 @@
+// Dependency analysis and tile planning of a queued loop chain (host only).
+//
+// arXiv 1709.02125, Sec. 3: loops of a chain are delayed; a dependency analysis
+// computes a skewed tiling schedule so that all data a tile uses stays in fast
+// memory for the whole tile. Sec. 4: the footprint of a tile, its overlap with the
+// neighbouring tiles ("left/right edge", "left/right footprint"), and which data
+// is uploaded / downloaded; Sec. 4.1: read-only data is not downloaded, write-first
+// data is not uploaded, and with the cyclic option write-first data is not
+// downloaded either.
+//
+// Tiling is along the slowest axis only (y in 2-D, z in 3-D). Loop i runs slow rows
+// [s_i(t), e_i(t)) in tile t; consecutive tiles of one loop partition its range.
+// The ends e_i(t) are computed by a backward sweep over the loops of the tile:
+//   RAW  a later reader j of D needs rows up to e_j + rmax_j(D) written first,
+//   WAR  a later writer j of D may not overwrite rows that loop i still reads in a
+//        later tile (those start at e_i(t) + rmin_i(D)), and
+//   WAW  a later writer's rows may not be overwritten later by an earlier writer,
+// which gives e_i >= max(b_t, RE[D] for D written, WE[D] for D written,
+// WE[D] - rmin_i(D) for D read), clipped to the loop's range, where RE / WE are the
+// maxima of e_j + rmax_j(D) over later readers and of e_j over later writers in the
+// same tile, and b_t is the nominal boundary of tile t. Every point is computed
+// exactly once, from the same inputs as in program order.
+//
+// Device residency: each dataset gets a cyclic slab of S rows (row y at slot
+// (y - y0) mod S) instead of the paper's three slots plus edge copy, so the overlap
+// between consecutive tiles never moves. S is the largest span of rows that are
+// live in one pipeline phase (see the phase rule in runtime.cu).
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "../../include/oc.h"
+#include "oc_internal.h"
+
+namespace oc {
+
+long long align_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+static inline uint64_t mix(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h * 0x100000001b3ull;
+}
+
+uint64_t chain_signature(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
+                         uint32_t flags)
+{
+    uint64_t h = 1469598103934665603ull;
+    h = mix(h, flags & (OC_FLAG_CYCLIC));
+    for (const Loop& lp : loops) {
+        h = mix(h, (uint64_t)lp.kernel);
+        h = mix(h, lp.params.size());
+        for (int a = 0; a < 3; ++a) { h = mix(h, (uint64_t)(uint32_t)lp.lo[a]); h = mix(h, (uint64_t)(uint32_t)lp.hi[a]); }
+        for (const Arg& ar : lp.args) {
+            h = mix(h, (uint64_t)ar.dat * 16 + ar.access);
+            if (ar.access != OC_REDUCE) {
+                const Dat& d = dats[ar.dat];
+                h = mix(h, (uint64_t)d.dtype * 1315423911ull + (uint64_t)d.nrows);
+            }
+            for (auto& o : ar.off)
+                h = mix(h, ((uint64_t)(uint16_t)o[0]) | ((uint64_t)(uint16_t)o[1] << 16) | ((uint64_t)(uint16_t)o[2] << 32));
+        }
+    }
+    return h;
+}
+
+bool full_row_write(const Loop& lp, const Dat& d)
+{
+    // A write covers whole slow rows if its range spans the full allocated extent of
+    // every non-slow axis (halo included), so no old value of the row survives.
+    for (int a = 0; a < d.ndim - 1; ++a)
+        if (lp.lo[a] > -d.hlo[a] || lp.hi[a] < d.size[a] + d.hhi[a]) return false;
+    return true;
+}
+
+static inline bool is_read(int acc) { return acc == OC_READ || acc == OC_RW; }
+static inline bool is_write(int acc) { return acc == OC_WRITE || acc == OC_RW; }
+
+bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
+                const std::vector<int>& red_ops, int h, int depth, uint32_t flags,
+                bool incore, Plan& P, std::string& err)
+{
+    P = Plan();
+    const int L = (int)loops.size();
+    P.L = L;
+    P.depth = depth;
+    const int k = depth - 2;  // upload lookahead in tiles
+    if (L == 0) { P.valid = true; P.T = 0; return true; }
+    const int nd = loops[0].ndim;
+    const int sa = nd - 1;
+
+    // datasets used, in first-use order
+    P.dat_index.assign(dats.size(), -1);
+    for (const Loop& lp : loops)
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && P.dat_index[ar.dat] < 0) {
+                P.dat_index[ar.dat] = (int)P.dp.size();
+                DatPlan dp;
+                dp.dat = ar.dat;
+                dp.y0 = dats[ar.dat].y0;
+                dp.nrows = dats[ar.dat].nrows;
+                P.dp.push_back(dp);
+            }
+    const int ND = (int)P.dp.size();
+
+    int Y0 = INT_MAX, Y1 = INT_MIN;
+    for (const Loop& lp : loops) { Y0 = std::min(Y0, lp.lo[sa]); Y1 = std::max(Y1, lp.hi[sa]); }
+    P.Y0 = Y0; P.Y1 = Y1;
+    const int span = std::max(1, Y1 - Y0);
+    if (h <= 0 || incore) h = span;
+    P.h = h;
+    const int T = (span + h - 1) / h;
+    P.T = T;
+    P.incore = incore;
+    P.se.assign((size_t)T * L * 2, 0);
+
+    // ---- skewed tiling: backward sweep per tile ------------------------------
+    std::vector<int> eprev(L);
+    for (int i = 0; i < L; ++i) eprev[i] = std::min(loops[i].lo[sa], loops[i].hi[sa]);
+    const long long NEG = LLONG_MIN / 4;
+    std::vector<long long> RE(ND), WE(ND);
+    for (int t = 0; t < T; ++t) {
+        std::fill(RE.begin(), RE.end(), NEG);
+        std::fill(WE.begin(), WE.end(), NEG);
+        const long long b = (t == T - 1) ? (long long)INT_MAX : (long long)Y0 + (long long)(t + 1) * h;
+        for (int i = L - 1; i >= 0; --i) {
+            const Loop& lp = loops[i];
+            long long e = b;
+            for (const Arg& ar : lp.args) {
+                if (ar.access == OC_REDUCE) continue;
+                int d = P.dat_index[ar.dat];
+                if (is_write(ar.access)) e = std::max(e, std::max(RE[d], WE[d]));
+                if (is_read(ar.access) && WE[d] > NEG) e = std::max(e, WE[d] - ar.rmin[sa]);
+            }
+            e = std::max(e, (long long)eprev[i]);
+            const int lo = std::min(lp.lo[sa], lp.hi[sa]), hi = lp.hi[sa];
+            e = std::min(std::max(e, (long long)lo), (long long)hi);
+            if (t == T - 1) e = hi;
+            P.se[((size_t)t * L + i) * 2] = eprev[i];
+            P.se[((size_t)t * L + i) * 2 + 1] = (int)e;
+            eprev[i] = (int)e;
+            for (const Arg& ar : lp.args) {
+                if (ar.access == OC_REDUCE) continue;
+                int d = P.dat_index[ar.dat];
+                if (is_read(ar.access)) RE[d] = std::max(RE[d], e + ar.rmax[sa]);
+                if (is_write(ar.access)) WE[d] = std::max(WE[d], e);
+            }
+        }
+    }
+
+    // ---- per-row first/last tile, upload and download need ----------------------
+    for (int d = 0; d < ND; ++d) {
+        DatPlan& dp = P.dp[d];
+        dp.first.assign(dp.nrows, -1);
+        dp.last.assign(dp.nrows, -1);
+        dp.need_up.assign(dp.nrows, 0);
+        dp.dl.assign(dp.nrows, 0);
+    }
+    auto mark = [&](DatPlan& dp, int t, long long a, long long b) {
+        a = std::max<long long>(a, dp.y0);
+        b = std::min<long long>(b, (long long)dp.y0 + dp.nrows);
+        for (long long y = a; y < b; ++y) {
+            int r = (int)(y - dp.y0);
+            if (dp.first[r] < 0) dp.first[r] = t;
+            dp.last[r] = t;
+        }
+    };
+    for (int t = 0; t < T; ++t)
+        for (int i = 0; i < L; ++i) {
+            int s = P.s(t, i), e = P.e(t, i);
+            if (s >= e) continue;
+            for (const Arg& ar : loops[i].args) {
+                if (ar.access == OC_REDUCE) continue;
+                DatPlan& dp = P.dp[P.dat_index[ar.dat]];
+                if (is_read(ar.access)) mark(dp, t, (long long)s + ar.rmin[sa], (long long)e + ar.rmax[sa]);
+                else mark(dp, t, s, e);
+            }
+        }
+    // program-order state per row: 0 untouched, 1 first access a full-row write,
+    // 2 first access anything else (a read or a partial write)
+    std::vector<std::vector<uint8_t>> state(ND), written(ND);
+    for (int d = 0; d < ND; ++d) { state[d].assign(P.dp[d].nrows, 0); written[d].assign(P.dp[d].nrows, 0); }
+    for (const Loop& lp : loops) {
+        int lo = lp.lo[sa], hi = lp.hi[sa];
+        if (lo >= hi) continue;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && is_read(ar.access)) {
+                int d = P.dat_index[ar.dat];
+                const DatPlan& dp = P.dp[d];
+                long long a = std::max<long long>((long long)lo + ar.rmin[sa], dp.y0);
+                long long b = std::min<long long>((long long)hi + ar.rmax[sa], (long long)dp.y0 + dp.nrows);
+                for (long long y = a; y < b; ++y) if (!state[d][y - dp.y0]) state[d][y - dp.y0] = 2;
+            }
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && is_write(ar.access)) {
+                int d = P.dat_index[ar.dat];
+                const DatPlan& dp = P.dp[d];
+                uint8_t st = full_row_write(lp, dats[ar.dat]) ? 1 : 2;
+                for (long long y = std::max(lo, dp.y0); y < std::min(hi, dp.y0 + dp.nrows); ++y) {
+                    if (!state[d][y - dp.y0]) state[d][y - dp.y0] = st;
+                    written[d][y - dp.y0] = 1;
+                }
+            }
+    }
+    const bool cyclic = (flags & OC_FLAG_CYCLIC) != 0;
+    for (int d = 0; d < ND; ++d) {
+        DatPlan& dp = P.dp[d];
+        for (int r = 0; r < dp.nrows; ++r) {
+            if (dp.first[r] < 0) continue;
+            dp.need_up[r] = state[d][r] == 2;
+            dp.dl[r] = written[d][r] && !(cyclic && state[d][r] == 1);
+        }
+        // group rows into per-tile intervals
+        auto group = [&](const std::vector<uint8_t>& need, const std::vector<int>& tile,
+                         std::vector<Interval>& out) {
+            out.clear();
+            int r = 0;
+            while (r < dp.nrows) {
+                if (!need[r]) { ++r; continue; }
+                int t = tile[r], a = r;
+                while (r < dp.nrows && need[r] && tile[r] == t) ++r;
+                out.push_back({t, a + dp.y0, r + dp.y0});
+            }
+            std::stable_sort(out.begin(), out.end(), [](const Interval& x, const Interval& y) { return x.t < y.t; });
+        };
+        group(dp.need_up, dp.first, dp.up);
+        group(dp.dl, dp.last, dp.down);
+
+        // slab rows: largest span of rows live in one phase. Phase p computes tile p,
+        // uploads tile p + k, downloads tile p - 1. A row is live from the phase of its
+        // upload (or first tile) to the phase of its download (or last tile).
+        if (incore) { dp.S = dp.nrows; continue; }
+        const int NP = T + k + 2;
+        std::vector<int> pmin(NP, INT_MAX), pmax(NP, INT_MIN);
+        for (int r = 0; r < dp.nrows; ++r) {
+            if (dp.first[r] < 0) continue;
+            int ps = dp.need_up[r] ? dp.first[r] - k : dp.first[r];
+            int pe = dp.dl[r] ? dp.last[r] + 1 : dp.last[r];
+            for (int p = ps; p <= pe; ++p) {
+                pmin[p + k] = std::min(pmin[p + k], r);
+                pmax[p + k] = std::max(pmax[p + k], r);
+            }
+        }
+        int S = 1;
+        for (int p = 0; p < NP; ++p)
+            if (pmax[p] >= pmin[p]) S = std::max(S, pmax[p] - pmin[p] + 1);
+        dp.S = std::min(S, dp.nrows);
+    }
+
+    // ---- reductions: per-row partials, grouped per handle --------------------------
+    P.loop_part.assign(L, -1);
+    P.loop_chunks.assign(L, 0);
+    P.loop_red.assign(L, -1);
+    P.loop_param.assign(L, 0);
+    std::vector<long long> loop_cnt(L, 0);
+    for (int i = 0; i < L; ++i)
+        for (const Arg& ar : loops[i].args)
+            if (ar.access == OC_REDUCE) {
+                int idx = -1;
+                for (size_t r = 0; r < P.rp.size(); ++r) if (P.rp[r].handle == ar.dat) idx = (int)r;
+                if (idx < 0) {
+                    RedPlan rp;
+                    rp.handle = ar.dat;
+                    rp.op = red_ops[ar.dat];
+                    idx = (int)P.rp.size();
+                    P.rp.push_back(rp);
+                }
+                P.loop_red[i] = idx;
+                long long plane = 1;
+                for (int a = 0; a < nd - 1; ++a) plane *= std::max(0, loops[i].hi[a] - loops[i].lo[a]);
+                int chunks = (int)std::max(1LL, (plane + kRedChunk - 1) / kRedChunk);
+                P.loop_chunks[i] = chunks;
+                loop_cnt[i] = plane > 0 ? (long long)std::max(0, loops[i].hi[sa] - loops[i].lo[sa]) * chunks : 0;
+            }
+    // ---- arena layout ---------------------------------------------------------------
+    long long off = 0;
+    for (int d = 0; d < ND; ++d) {
+        DatPlan& dp = P.dp[d];
+        dp.off = off;
+        off += align_up((long long)dp.S * dats[dp.dat].row_bytes(), 256);
+    }
+    P.slab_bytes = off;
+    off = 0;
+    for (size_t r = 0; r < P.rp.size(); ++r) {
+        P.rp[r].part_off = off;
+        long long c = 0;
+        for (int i = 0; i < L; ++i)
+            if (P.loop_red[i] == (int)r) { P.loop_part[i] = off + c * 8; c += loop_cnt[i]; }
+        P.rp[r].count = c;
+        off += align_up(std::max(1LL, c) * 8, 256);
+    }
+    int np = 0;
+    for (int i = 0; i < L; ++i) { P.loop_param[i] = np; np += (int)loops[i].params.size(); }
+    P.nparams = np;
+    P.params_off = off;
+    off += align_up(std::max(1, np) * 8, 256);
+    P.results_off = off;
+    off += align_up(std::max<long long>(1, (long long)P.rp.size()) * 8, 256);
+    P.scratch_bytes = off;
+    P.arena_bytes = P.slab_bytes + P.scratch_bytes;
+    P.sig = chain_signature(loops, dats, flags) ^ ((uint64_t)h * 0x9E3779B1u) ^ ((uint64_t)depth << 56)
+            ^ (incore ? 0x5555ull : 0);
+    P.valid = true;
+    (void)err;
+    return true;
+}
+
+int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
+                    const std::vector<int>& red_ops, int depth, uint32_t flags,
+                    long long budget, std::string& err)
+{
+    if (loops.empty()) return 1;
+    const int sa = loops[0].ndim - 1;
+    int Y0 = INT_MAX, Y1 = INT_MIN;
+    for (const Loop& lp : loops) { Y0 = std::min(Y0, lp.lo[sa]); Y1 = std::max(Y1, lp.hi[sa]); }
+    const int span = std::max(1, Y1 - Y0);
+    Plan P;
+    auto fits = [&](int h) {
+        build_plan(loops, dats, red_ops, h, depth, flags, false, P, err);
+        return P.arena_bytes <= budget;
+    };
+    if (!fits(1)) return 0;
+    if (fits(span)) return span;
+    int lo = 1, hi = span;  // fits(lo), !fits(hi)
+    while (hi - lo > 1) {
+        int mid = lo + (hi - lo) / 2;
+        if (fits(mid)) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace oc

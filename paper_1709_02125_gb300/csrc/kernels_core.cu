@@ -1,0 +1,286 @@
+// Generic stencil-loop kernels of the executor: COPY, LINCOMB, REDUCE (with the
+// deterministic partial combine) and the compensated HILO_ADD update.
+//
+// arXiv 1709.02125, Sec. 3: a parallel loop applies a kernel at every point of its
+// range; points are independent, so each thread owns one x column and R consecutive
+// slow rows of the tile. Datasets are read through their cyclic slab (launch.h):
+// the slot of a row is advanced with one compare-and-subtract per row, never a
+// modulo. x is the fastest axis, so a warp reads 32 consecutive elements of one
+// x-line (coalesced); rows of neighbouring samples are shared through L1/L2.
+//
+// Arithmetic follows the evaluation order stated in include/oc.h for every point;
+// the library is compiled with -fmad=false so no multiply-add is contracted and the
+// FP64 results are bit-identical to any IEEE implementation of the same order.
+#include <cuda_runtime.h>
+
+#include "../../include/oc.h"
+#include "launch.h"
+
+namespace oc {
+
+namespace {
+
+constexpr int kThreadsX = 128;
+constexpr int kRows = 4;
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Pointer to element (x + dx, yl + dy) of the x-line of slot `slot`.
+template <typename T>
+__device__ __forceinline__ const T* col_ptr(const DView& v, int x, int yl)
+{
+    if (v.periodic & 1) x = wrap1(x, v.nx);
+    if (v.periodic & 2) yl = wrap1(yl, v.ny);
+    return reinterpret_cast<const T*>(v.base) + (long long)(yl + v.oy) * v.pitch + v.ox + x;
+}
+
+__device__ __forceinline__ int first_slot(const DView& v, int s)
+{
+    int slot = v.slot0 + (s - v.W0);
+    return slot >= v.S ? slot - v.S : slot;
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const int yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int s0 = d.lo[sa] + (int)blockIdx.z * R;
+    const int shi = d.hi[sa];
+    const int M = d.nsamp;
+
+    T acc[R], x0[R], x1[R], x2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc[r] = T(0); x0[r] = x1[r] = x2[r] = T(0); }
+
+    for (int m = 0; m < M; ++m) {
+        const DView& v = d.v[d.sarg[m]];
+        const T c = (T)d.params[1 + m];
+        const T* col = col_ptr<T>(v, x + d.soff[m][0], yl + (d.ndim == 3 ? d.soff[m][1] : 0));
+        int slot = first_slot(v, s0 + d.soff[m][sa]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T val = T(0);
+            if (s0 + r < shi) val = __ldg(col + (long long)slot * v.row_elems);
+            if (++slot == v.S) slot = 0;
+            if (m == 0) { acc[r] = c * val; x0[r] = val; }
+            else {
+                acc[r] = acc[r] + c * val;
+                if (m == 1) x1[r] = val;
+                if (m == 2) x2[r] = val;
+            }
+        }
+    }
+    const T alpha = (T)d.params[0];
+    if (alpha != T(0)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T a = x0[r];
+            const T b = M > 1 ? x1[r] : x0[r];
+            const T c = M > 2 ? x2[r] : x0[r];
+            acc[r] = acc[r] + ((alpha * a) * b) / (T(1) + c * c);
+        }
+    }
+    const DView& o = d.v[0];
+    T* ocol = const_cast<T*>(col_ptr<T>(o, x, yl));
+    int slot = first_slot(o, s0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (s0 + r < shi) ocol[(long long)slot * o.row_elems] = acc[r];
+        if (++slot == o.S) slot = 0;
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreadsX) k_copy(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const int yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int s0 = d.lo[sa] + (int)blockIdx.z * R;
+    const int shi = d.hi[sa];
+    const DView& v = d.v[1];
+    const T* col = col_ptr<T>(v, x + d.soff[0][0], yl + (d.ndim == 3 ? d.soff[0][1] : 0));
+    int slot = first_slot(v, s0 + d.soff[0][sa]);
+    T val[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        val[r] = T(0);
+        if (s0 + r < shi) val[r] = __ldg(col + (long long)slot * v.row_elems);
+        if (++slot == v.S) slot = 0;
+    }
+    const DView& o = d.v[0];
+    T* ocol = const_cast<T*>(col_ptr<T>(o, x, yl));
+    slot = first_slot(o, s0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (s0 + r < shi) ocol[(long long)slot * o.row_elems] = val[r];
+        if (++slot == o.S) slot = 0;
+    }
+}
+
+// (hi, lo) += (float)scale * du, compensated (TwoSum, then Fast2Sum renormalisation).
+template <int R>
+__global__ void __launch_bounds__(kThreadsX) k_hilo_add(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const int yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int s0 = d.lo[sa] + (int)blockIdx.z * R;
+    const int shi = d.hi[sa];
+    const float scale = (float)d.params[0];
+    float* hp = const_cast<float*>(col_ptr<float>(d.v[0], x, yl));
+    float* lp = const_cast<float*>(col_ptr<float>(d.v[1], x, yl));
+    const float* up = col_ptr<float>(d.v[2], x, yl);
+    int sh = first_slot(d.v[0], s0), sl = first_slot(d.v[1], s0), su = first_slot(d.v[2], s0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (s0 + r < shi) {
+            const long long ih = (long long)sh * d.v[0].row_elems;
+            const long long il = (long long)sl * d.v[1].row_elems;
+            const float hi = hp[ih], lo = lp[il];
+            const float y = scale * __ldg(up + (long long)su * d.v[2].row_elems);
+            const float s = hi + y;
+            const float z = s - hi;
+            const float e = (hi - (s - z)) + (y - z);
+            const float l = lo + e;
+            const float h2 = s + l;
+            hp[ih] = h2;
+            lp[il] = l - (h2 - s);
+        }
+        if (++sh == d.v[0].S) sh = 0;
+        if (++sl == d.v[1].S) sl = 0;
+        if (++su == d.v[2].S) su = 0;
+    }
+}
+
+__device__ __forceinline__ double red_identity(int op)
+{
+    return op == OC_SUM ? 0.0 : (op == OC_MAX ? -__longlong_as_double(0x7ff0000000000000LL)
+                                              : __longlong_as_double(0x7ff0000000000000LL));
+}
+
+__device__ __forceinline__ double red_apply(int op, double a, double b)
+{
+    if (op == OC_SUM) return a + b;
+    if (op == OC_MAX) return b > a ? b : a;
+    return b < a ? b : a;
+}
+
+constexpr int kRedThreads = 256;
+
+// Fixed-shape block fold: each thread folds its strided elements in order, then a
+// fixed shuffle tree per warp and a fixed tree over the warps.
+__device__ __forceinline__ double block_fold(double acc, int op)
+{
+    __shared__ double sm[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = acc;
+    __syncthreads();
+    if (w == 0) {
+        acc = l < kRedThreads / 32 ? sm[l] : red_identity(op);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
+    }
+    return acc;
+}
+
+// One block per (chunk of kRedChunk points of a slow row, slow row). The partial of
+// row s, chunk c is stored at part[(s - part_row0) * chunks + c], independent of the
+// tiling, so tiled and untiled runs fold the same partials in the same order.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ LaunchDesc d)
+{
+    const int sa = d.ndim - 1;
+    const int s = d.lo[sa] + (int)blockIdx.y;
+    const int nxr = d.hi[0] - d.lo[0];
+    const long long plane = d.ndim == 3 ? (long long)nxr * (d.hi[1] - d.lo[1]) : (long long)nxr;
+    const long long q0 = (long long)blockIdx.x * 4096;
+    const long long q1 = q0 + 4096 < plane ? q0 + 4096 : plane;
+    const int op = d.red_op;
+    const int mode = (int)d.params[0];
+    const bool two = d.nargs == 3;
+    const DView& a = d.v[0];
+    const DView& b = d.v[1];
+    const int sla = first_slot(a, s);
+    const int slb = two ? first_slot(b, s) : 0;
+    double acc = red_identity(op);
+    for (long long q = q0 + threadIdx.x; q < q1; q += kRedThreads) {
+        const int x = d.lo[0] + (int)(q % nxr);
+        const int yl = d.ndim == 3 ? d.lo[1] + (int)(q / nxr) : 0;
+        double v = (double)*(col_ptr<T>(a, x, yl) + (long long)sla * a.row_elems);
+        if (two) v = v + (double)*(col_ptr<T>(b, x, yl) + (long long)slb * b.row_elems);
+        if (mode == 1) v = fabs(v);
+        else if (mode == 2) v = v * v;
+        acc = red_apply(op, acc, v);
+    }
+    acc = block_fold(acc, op);
+    if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_combine(const double* __restrict__ part, long long n,
+                                                        int op, double* out)
+{
+    const long long per = (n + kRedThreads - 1) / kRedThreads;
+    const long long a = per * threadIdx.x;
+    const long long b = a + per < n ? a + per : n;
+    double acc = red_identity(op);
+    for (long long i = a; i < b; ++i) acc = red_apply(op, acc, part[i]);
+    acc = block_fold(acc, op);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+template <typename F>
+cudaError_t launch_pointwise(const LaunchDesc& d, cudaStream_t st, F kern)
+{
+    const int sa = d.ndim - 1;
+    const int nx = d.hi[0] - d.lo[0];
+    const int ns = d.hi[sa] - d.lo[sa];
+    if (nx <= 0 || ns <= 0 || (d.ndim == 3 && d.hi[1] <= d.lo[1])) return cudaSuccess;
+    dim3 grid((nx + kThreadsX - 1) / kThreadsX, d.ndim == 3 ? d.hi[1] - d.lo[1] : 1,
+              (ns + kRows - 1) / kRows);
+    kern<<<grid, kThreadsX, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
+{
+    const bool f32 = d.dtype == OC_F32;
+    switch (d.kernel) {
+    case OC_K_COPY:
+        return f32 ? launch_pointwise(d, st, k_copy<float, kRows>) : launch_pointwise(d, st, k_copy<double, kRows>);
+    case OC_K_LINCOMB:
+        return f32 ? launch_pointwise(d, st, k_lincomb<float, kRows>) : launch_pointwise(d, st, k_lincomb<double, kRows>);
+    case OC_K_HILO_ADD:
+        return launch_pointwise(d, st, k_hilo_add<kRows>);
+    case OC_K_REDUCE: {
+        const int sa = d.ndim - 1;
+        const int ns = d.hi[sa] - d.lo[sa];
+        if (ns <= 0) return cudaSuccess;
+        dim3 grid(d.chunks, ns, 1);
+        if (f32) k_reduce<float><<<grid, kRedThreads, 0, st>>>(d);
+        else k_reduce<double><<<grid, kRedThreads, 0, st>>>(d);
+        return cudaGetLastError();
+    }
+    default:
+        return launch_physics(d, st);
+    }
+}
+
+cudaError_t launch_combine(const double* part, long long n, int op, double* out, cudaStream_t st)
+{
+    k_combine<<<1, kRedThreads, 0, st>>>(part, n, op, out);
+    return cudaGetLastError();
+}
+
+int kernels_compiled_arch() { return 1030; }
+
+}  // namespace oc

@@ -1,0 +1,58 @@
+// Launch descriptors passed from the executor (runtime.cu) to the kernels.
+// Plain structs: device pointers, sizes and per-launch constants only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace oc {
+
+constexpr int kLaunchMaxArgs = 24;
+constexpr int kLaunchMaxSamples = 64;
+
+// Device view of one dataset argument inside one launch. A slow row s lives at
+// slab slot  slot0 + (s - W0)  (minus S if >= S); every row a launch touches lies in
+// [W0, W0 + S), so one conditional subtraction replaces the modulo. Element
+// (x, yl, s) is at base + slot*row_elems + (yl + oy)*pitch + ox + x, where yl is the
+// y index of a 3-D dataset (0 in 2-D).
+struct DView {
+    char* base;
+    long long row_elems;
+    long long pitch;
+    int ox, oy;
+    int S, W0, slot0;
+    int nx, ny;        // interior extents of the two fast axes (periodic wrap)
+    int periodic;      // bit 0: x wraps modulo nx, bit 1 (3-D): y wraps modulo ny
+    int pad_;
+};
+
+struct LaunchDesc {
+    int kernel;
+    int ndim;
+    int dtype;                 // 0 = f64, 1 = f32 (all dataset arguments share it)
+    int lo[3], hi[3];          // iteration range of this launch; slow axis = this tile's rows
+    int nargs;
+    int npts[kLaunchMaxArgs];  // stencil points per argument
+    int access[kLaunchMaxArgs];
+    DView v[kLaunchMaxArgs];
+    int nsamp;                 // total stencil samples of the READ arguments
+    int sarg[kLaunchMaxSamples];
+    int soff[kLaunchMaxSamples][3];
+    const double* params;      // device pointer to this loop's parameters
+    int nparams;
+    double* part;              // reduction partials of this loop (row part_row0 first)
+    int part_row0;
+    int chunks;                // partials per slow row
+    int red_op;                // OC_SUM / OC_MAX / OC_MIN
+};
+
+// Launch one loop tile on `stream`. Returns cudaSuccess or the launch error.
+cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t stream);
+// Fold `n` partials of one reduction into *out (deterministic, single block).
+cudaError_t launch_combine(const double* part, long long n, int op, double* out,
+                           cudaStream_t stream);
+// Launch a PDE kernel (Euler / Navier-Stokes ids); kernels_physics.cu.
+cudaError_t launch_physics(const LaunchDesc& d, cudaStream_t stream);
+int kernels_compiled_arch();
+
+}  // namespace oc

@@ -1,0 +1,1185 @@
+// Executor and C ABI of liboc: dataset stores, the lazy loop queue, plan selection,
+// and the three-stream tile pipeline.
+//
+// arXiv 1709.02125, Sec. 3 (lazy loop chains, data owned by the library), Sec. 4,
+// Algorithm 1 (explicitly managed tiling with three streams) and Sec. 4.1 (copy
+// avoidance, cyclic option, speculative prefetch).
+//
+// Pipeline. With upload lookahead k = depth - 2, phase p (p = -k .. T) uploads tile
+// p + k on stream 1, computes tile p on stream 0 and downloads tile p - 1 on stream
+// 2. A slab row is live from the phase of its upload (or of its first tile, if it is
+// not uploaded) to the phase of its download (or of its last tile). Slabs are sized
+// (analysis.cpp) so that rows live in the same phase never share a slot; an
+// operation of phase p that overwrites slots therefore only has to wait for the
+// operations of phases <= p - 1 on the other streams:
+//   upload  (phase p): waits compute(p - 1) and download of tile p - 2;
+//   compute (tile p) : waits upload(p) and download of tile p - 2;
+//   download(tile p) : waits compute(p).
+// Rows shared by consecutive tiles stay in their slot, which replaces the paper's
+// right-edge to left-edge copy between slots (Algorithm 1, finishing phase).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/oc.h"
+#include "launch.h"
+#include "oc_internal.h"
+#include "physics.h"
+#include "planner.h"
+
+namespace oc {
+
+static char g_err[1024] = "";
+
+static int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define OC_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(OC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+// One profiled launch: events bracketing it on the compute stream.
+struct ProfRec {
+    int kernel;
+    double bytes, points;
+    cudaEvent_t a, b;
+};
+
+struct KStat {
+    long long launches = 0;
+    double ms = 0, bytes = 0, points = 0;
+};
+
+struct GraphSet {
+    std::vector<cudaGraphExec_t> tiles;
+    std::vector<std::vector<ProfRec>> prof;  // events captured into each tile's graph
+};
+
+struct Prefetch {
+    bool active = false;
+    uint64_t sig = 0;
+    std::vector<std::vector<Interval>> rows;  // per plan dataset index
+    double bytes = 0;
+};
+
+struct Ctx {
+    uint32_t flags = 0;
+    int planner_mode = OC_PLAN_FIXED;
+    bool dryrun = false;
+    long long budget = 0;
+    char* arena = nullptr;
+    long long arena_bytes = 0;
+    bool own_arena = false;
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    bool own_streams = false;
+    std::vector<Dat> dats;
+    std::vector<int> red_ops;
+    std::vector<double> red_val;
+    std::vector<char> red_has;
+    std::vector<Loop> queue;
+    std::unordered_map<uint64_t, Plan> plans;       // by plan signature
+    std::unordered_map<uint64_t, std::pair<int, int>> choice;  // chain signature -> (h, depth)
+    std::unordered_map<uint64_t, std::vector<std::vector<LaunchDesc>>> descs;  // plan sig -> tiles
+    std::unordered_map<uint64_t, GraphSet> graphs;
+    const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
+    int force_h = 0, force_depth = 0;
+    std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
+    cudaEvent_t ev_pf = nullptr, ev_end = nullptr;
+    double* h_params = nullptr;
+    size_t h_params_cap = 0;
+    double* h_results = nullptr;
+    size_t h_results_cap = 0;
+    Prefetch pf;
+    bool resident_mode = false;
+    long long resident_bytes = 0;
+    double timeout_s = 600.0;
+    oc_stats_t stats{};
+    // profiling (OC_FLAG_PROFILE)
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    std::vector<ProfRec> prof_pending;
+    std::unordered_map<int, KStat> kstats;
+};
+
+static Ctx* g = nullptr;
+
+// ---------------------------------------------------------------------------------
+static int wait_event(cudaEvent_t ev, double timeout_s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return OC_OK;
+        if (e != cudaErrorNotReady)
+            return fail(OC_ERR_CUDA, "event wait failed: %s", cudaGetErrorString(e));
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(OC_ERR_TIMEOUT, "bounded wait expired after %.1f s", el);
+        if (el > 1e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+static int wait_stream(cudaStream_t s)
+{
+    OC_CUDA(cudaEventRecord(g->ev_end, s));
+    return wait_event(g->ev_end, g->timeout_s);
+}
+
+static int ensure_events(int T)
+{
+    while ((int)g->ev_up.size() < T) {
+        cudaEvent_t a, b, c;
+        OC_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        OC_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+        OC_CUDA(cudaEventCreateWithFlags(&c, cudaEventDisableTiming));
+        g->ev_up.push_back(a);
+        g->ev_comp.push_back(b);
+        g->ev_down.push_back(c);
+    }
+    return OC_OK;
+}
+
+static void* host_alloc(size_t bytes, bool pinned)
+{
+    void* p = nullptr;
+    if (pinned) {
+        if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        return p;
+    }
+    return malloc(bytes);
+}
+
+static void host_free(void* p, bool pinned)
+{
+    if (!p) return;
+    if (pinned) cudaFreeHost(p);
+    else free(p);
+}
+
+// ---------------------------------------------------------------------------------
+// Copies between the pinned store and a slab. Rows [a, b) of dataset d go to slots
+// (y - y0) mod S of the slab at `slab`; a range crossing the slab end is split.
+static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cudaStream_t s,
+                     double& bytes)
+{
+    const long long rb = d.row_bytes();
+    while (a < b) {
+        int slot = (int)(((long long)(a - d.y0)) % S);
+        int n = std::min(b - a, S - slot);
+        char* dev = slab + (long long)slot * rb;
+        char* host = (char*)d.host + (long long)(a - d.y0) * rb;
+        if (up) OC_CUDA(cudaMemcpyAsync(dev, host, (size_t)n * rb, cudaMemcpyHostToDevice, s));
+        else OC_CUDA(cudaMemcpyAsync(host, dev, (size_t)n * rb, cudaMemcpyDeviceToHost, s));
+        bytes += (double)n * rb;
+        a += n;
+    }
+    return OC_OK;
+}
+
+// Subtract prefetched rows from an upload interval; emit the remainder.
+template <typename F>
+static int for_missing(const Interval& iv, const std::vector<Interval>* have, F emit)
+{
+    int a = iv.a;
+    if (have) {
+        for (const Interval& h : *have) {
+            if (h.b <= a || h.a >= iv.b) continue;
+            if (h.a > a) { int r = emit(a, h.a); if (r) return r; }
+            a = std::max(a, h.b);
+        }
+    }
+    if (a < iv.b) return emit(a, iv.b);
+    return OC_OK;
+}
+
+// ---------------------------------------------------------------------------------
+static DView make_view(const Dat& d, char* slab, int S, int W0)
+{
+    DView v;
+    v.base = slab;
+    v.row_elems = d.row_elems;
+    v.pitch = d.pitch;
+    v.ox = d.ox;
+    v.oy = d.ndim == 3 ? d.hlo[1] : 0;
+    v.S = S;
+    if (W0 < d.y0) W0 = d.y0;
+    v.W0 = W0;
+    v.slot0 = (int)(((long long)(W0 - d.y0)) % S);
+    v.nx = d.size[0];
+    v.ny = d.ndim == 3 ? d.size[1] : 1;
+    v.periodic = 0;
+    if (d.periodic & 1) v.periodic |= 1;
+    if (d.ndim == 3 && (d.periodic & 2)) v.periodic |= 2;
+    v.pad_ = 0;
+    return v;
+}
+
+static char* slab_base(const Plan& P, int di)
+{
+    const DatPlan& dp = P.dp[di];
+    const Dat& d = g->dats[dp.dat];
+    if (P.incore && d.resident) return g->arena + d.res_off;
+    return g->arena + dp.off;
+}
+
+static long long scratch_base(const Plan& P)
+{
+    return P.incore ? g->resident_bytes : P.slab_bytes;
+}
+
+static void build_descs(const Plan& P, const std::vector<Loop>& loops,
+                        std::vector<std::vector<LaunchDesc>>& out)
+{
+    out.assign(P.T, {});
+    const long long sb = scratch_base(P);
+    for (int t = 0; t < P.T; ++t)
+        for (int i = 0; i < P.L; ++i) {
+            int s = P.s(t, i), e = P.e(t, i);
+            const Loop& lp = loops[i];
+            if (s >= e || lp.points() == 0) continue;
+            const int sa = lp.ndim - 1;
+            LaunchDesc d;
+            memset(&d, 0, sizeof(d));
+            d.kernel = lp.kernel;
+            d.ndim = lp.ndim;
+            for (int a = 0; a < 3; ++a) { d.lo[a] = lp.lo[a]; d.hi[a] = lp.hi[a]; }
+            d.lo[sa] = s;
+            d.hi[sa] = e;
+            d.nargs = (int)lp.args.size();
+            d.dtype = -1;
+            int ns = 0;
+            for (int j = 0; j < d.nargs; ++j) {
+                const Arg& ar = lp.args[j];
+                d.access[j] = ar.access;
+                d.npts[j] = (int)ar.off.size();
+                if (ar.access == OC_REDUCE) continue;
+                const Dat& dd = g->dats[ar.dat];
+                if (d.dtype < 0) d.dtype = dd.dtype;
+                int di = P.dat_index[ar.dat];
+                int W0 = (ar.access == OC_READ || ar.access == OC_RW) ? s + ar.rmin[sa] : s;
+                if (ar.access == OC_RW) W0 = std::min(W0, s);
+                d.v[j] = make_view(dd, slab_base(P, di), P.dp[di].S, W0);
+                if (ar.access == OC_READ && j >= 1)
+                    for (auto& o : ar.off) {
+                        if (ns < kLaunchMaxSamples) {
+                            d.sarg[ns] = j;
+                            d.soff[ns][0] = o[0]; d.soff[ns][1] = o[1]; d.soff[ns][2] = o[2];
+                        }
+                        ++ns;
+                    }
+            }
+            if (lp.kernel == OC_K_REDUCE) ns = 0;
+            d.nsamp = ns;
+            d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
+            d.nparams = (int)lp.params.size();
+            if (P.loop_red[i] >= 0) {
+                d.part = (double*)(g->arena + sb + P.loop_part[i]);
+                d.part_row0 = std::min(lp.lo[sa], lp.hi[sa]);
+                d.chunks = P.loop_chunks[i];
+                d.red_op = P.rp[P.loop_red[i]].op;
+            }
+            if (d.dtype < 0) d.dtype = OC_F64;
+            out[t].push_back(d);
+        }
+}
+
+static double launch_bytes(const LaunchDesc& d, double& points)
+{
+    points = 1;
+    for (int a = 0; a < d.ndim; ++a) points *= (double)std::max(0, d.hi[a] - d.lo[a]);
+    double b = 0;
+    const double esz = d.dtype == OC_F32 ? 4 : 8;
+    for (int j = 0; j < d.nargs; ++j)
+        if (d.access[j] != OC_REDUCE) b += points * esz * (d.access[j] == OC_RW ? 2 : 1);
+    return b;
+}
+
+static int pool_event(cudaEvent_t& ev, bool persistent)
+{
+    if (!persistent && g->ev_next < g->ev_pool.size()) { ev = g->ev_pool[g->ev_next++]; return OC_OK; }
+    OC_CUDA(cudaEventCreate(&ev));
+    if (!persistent) { g->ev_pool.push_back(ev); g->ev_next = g->ev_pool.size(); }
+    return OC_OK;
+}
+
+// Launch the kernels of one tile; with profiling, bracket each with events. `recs`
+// receives the records (persistent events when the launches are being captured).
+static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
+                            std::vector<ProfRec>* recs = nullptr, bool persistent = false)
+{
+    const bool prof = (g->flags & OC_FLAG_PROFILE) != 0;
+    for (const LaunchDesc& d : ds) {
+        ProfRec pr{};
+        if (prof) {
+            int r = pool_event(pr.a, persistent);
+            if (!r) r = pool_event(pr.b, persistent);
+            if (r) return r;
+            pr.kernel = d.kernel;
+            pr.bytes = launch_bytes(d, pr.points);
+            OC_CUDA(cudaEventRecord(pr.a, s));
+        }
+        cudaError_t e = launch_loop(d, s);
+        if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", d.kernel, cudaGetErrorString(e));
+        if (prof) {
+            OC_CUDA(cudaEventRecord(pr.b, s));
+            if (recs) recs->push_back(pr);
+            else g->prof_pending.push_back(pr);
+        }
+    }
+    return OC_OK;
+}
+
+// After a chain has completed: fold the profiled launches into the per-kernel totals.
+static int collect_profile()
+{
+    for (const ProfRec& pr : g->prof_pending) {
+        float ms = 0;
+        OC_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
+        KStat& k = g->kstats[pr.kernel];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += pr.bytes;
+        k.points += pr.points;
+    }
+    g->prof_pending.clear();
+    g->ev_next = 0;
+    return OC_OK;
+}
+
+static int count_launches(const std::vector<LaunchDesc>& ds) { return (int)ds.size(); }
+
+// ---------------------------------------------------------------------------------
+static long long resident_total()
+{
+    long long tot = 0;
+    for (const Dat& d : g->dats) tot += align_up(d.bytes(), 256);
+    return tot;
+}
+
+static int leave_resident_mode()
+{
+    for (Dat& d : g->dats) {
+        if (d.resident && !d.host_valid && d.dev_valid && !g->dryrun) {
+            OC_CUDA(cudaMemcpyAsync(d.host, g->arena + d.res_off, (size_t)d.bytes(),
+                                    cudaMemcpyDeviceToHost, g->st[2]));
+        }
+    }
+    if (!g->dryrun) { int r = wait_stream(g->st[2]); if (r) return r; }
+    for (Dat& d : g->dats) { d.resident = false; d.dev_valid = false; d.host_valid = true; d.res_off = -1; }
+    g->resident_mode = false;
+    return OC_OK;
+}
+
+static void enter_resident_layout()
+{
+    long long off = 0;
+    for (Dat& d : g->dats) {
+        if (!d.resident) { d.resident = true; d.dev_valid = false; }
+        d.res_off = off;
+        off += align_up(d.bytes(), 256);
+    }
+    g->resident_bytes = off;
+    g->resident_mode = true;
+}
+
+// Refresh the halo rows of a periodic slow axis from the opposite end (deep ghosts).
+static int ghost_fill_host(const Dat& d)
+{
+    const int sa = d.slow();
+    const int n = d.size[sa], lo = d.hlo[sa], hi = d.hhi[sa];
+    const long long rb = d.row_bytes();
+    char* h = (char*)d.host;
+    auto row = [&](int y) { return h + (long long)(y - d.y0) * rb; };
+    for (int y = -lo; y < 0; ++y) memcpy(row(y), row(y + n), rb);
+    for (int y = n; y < n + hi; ++y) memcpy(row(y), row(y - n), rb);
+    return OC_OK;
+}
+
+static int ghost_fill_device(const Dat& d, cudaStream_t s)
+{
+    const int sa = d.slow();
+    const int n = d.size[sa], lo = d.hlo[sa], hi = d.hhi[sa];
+    const long long rb = d.row_bytes();
+    char* b = g->arena + d.res_off;
+    if (lo > 0) OC_CUDA(cudaMemcpyAsync(b, b + (long long)n * rb, (size_t)lo * rb, cudaMemcpyDeviceToDevice, s));
+    if (hi > 0) OC_CUDA(cudaMemcpyAsync(b + (long long)(n + lo) * rb, b + (long long)lo * rb, (size_t)hi * rb,
+                                        cudaMemcpyDeviceToDevice, s));
+    return OC_OK;
+}
+
+static bool reads_ghosts(const Plan& P, int di)
+{
+    const DatPlan& dp = P.dp[di];
+    const Dat& d = g->dats[dp.dat];
+    const int sa = d.slow();
+    for (int r = 0; r < dp.nrows; ++r) {
+        int y = r + dp.y0;
+        if ((y < 0 || y >= d.size[sa]) && dp.first[r] >= 0) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------------
+static int select_plan(const std::vector<Loop>& loops, Plan*& out)
+{
+    std::string err;
+    const uint64_t csig = chain_signature(loops, g->dats, g->flags);
+    // in-core (resident) mode when every declared dataset fits with the scratch
+    Plan inc;
+    build_plan(loops, g->dats, g->red_ops, 0, 3, g->flags, true, inc, err);
+    const long long rtot = resident_total();
+    if (rtot + inc.scratch_bytes <= g->budget && g->force_h == 0) {
+        if (!g->resident_mode) enter_resident_layout();
+        else {  // new datasets since the layout was made
+            long long off = 0;
+            for (Dat& d : g->dats) {
+                if (!d.resident) { d.resident = true; d.dev_valid = false; d.res_off = off; }
+                off = std::max(off, d.res_off + align_up(d.bytes(), 256));
+            }
+            g->resident_bytes = off;
+        }
+        uint64_t key = inc.sig ^ 0x1234567ull ^ ((uint64_t)g->resident_bytes * 0x9E3779B97F4A7C15ull);
+        auto it = g->plans.find(key);
+        if (it == g->plans.end()) { inc.sig = key; it = g->plans.emplace(key, std::move(inc)).first; }
+        out = &it->second;
+        return OC_OK;
+    }
+    if (g->resident_mode) { int r = leave_resident_mode(); if (r) return r; }
+
+    int h = 0, depth = 3;
+    auto ch = g->choice.find(csig);
+    if (g->force_h > 0 || g->force_depth > 0 || ch == g->choice.end()) {
+        depth = g->force_depth > 0 ? g->force_depth : 3;
+        if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED) {
+            int ph = 0, pd = 0;
+            if (planner_choose(loops, g->dats, g->red_ops, g->flags, g->budget, g->planner_mode, ph, pd)) {
+                h = ph; depth = pd;
+            }
+        }
+        if (h <= 0) {
+            if (g->force_h > 0) h = g->force_h;
+            else h = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
+        }
+        if (h <= 0) return fail(OC_ERR_BUDGET, "device budget of %lld bytes cannot hold one tile of height 1", g->budget);
+        if (g->force_h <= 0 && g->force_depth <= 0) g->choice[csig] = {h, depth};
+    } else {
+        h = ch->second.first;
+        depth = ch->second.second;
+    }
+    Plan P;
+    build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err);
+    if (P.arena_bytes > g->budget)
+        return fail(OC_ERR_BUDGET, "plan with tile height %d depth %d needs %lld bytes > budget %lld", h,
+                    depth, P.arena_bytes, g->budget);
+    auto it = g->plans.find(P.sig);
+    if (it == g->plans.end()) it = g->plans.emplace(P.sig, std::move(P)).first;
+    out = &it->second;
+    return OC_OK;
+}
+
+// Prefetch the first tile of a chain assumed to repeat this plan (Sec. 4.1). Only
+// rows whose host copy is final before the last download phase and whose slots are
+// not live in the last two phases are fetched; ghost rows of a periodic slow axis
+// are left out (they are refreshed when the next chain starts).
+static int issue_prefetch(const Plan& P)
+{
+    g->pf.active = false;
+    g->pf.rows.assign(P.dp.size(), {});
+    g->pf.bytes = 0;
+    if (P.T < 2 || P.incore) return OC_OK;
+    const int T = P.T;
+    OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_comp[T - 1], 0));
+    OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 2], 0));
+    bool any = false;
+    for (size_t di = 0; di < P.dp.size(); ++di) {
+        const DatPlan& dp = P.dp[di];
+        const Dat& d = g->dats[dp.dat];
+        const int sa = d.slow();
+        // slots live in phases T-1 and T
+        std::vector<uint8_t> busy(dp.S, 0);
+        for (int r = 0; r < dp.nrows; ++r) {
+            if (dp.first[r] < 0) continue;
+            int pe = dp.dl[r] ? dp.last[r] + 1 : dp.last[r];
+            if (pe >= T - 1) busy[r % dp.S] = 1;
+        }
+        bool ok = true;
+        std::vector<Interval> rows;
+        for (const Interval& iv : dp.up) {
+            if (iv.t != 0) continue;
+            for (int y = iv.a; y < iv.b; ++y) {
+                int r = y - dp.y0;
+                bool ghost = (d.periodic & (1 << sa)) && (y < 0 || y >= d.size[sa]);
+                if (ghost) continue;
+                if (busy[r % dp.S] || (dp.dl[r] && dp.last[r] >= T - 1)) { ok = false; break; }
+                if (!rows.empty() && rows.back().b == y) rows.back().b = y + 1;
+                else rows.push_back({0, y, y + 1});
+            }
+            if (!ok) break;
+        }
+        if (!ok) continue;
+        for (const Interval& iv : rows) {
+            double b = 0;
+            int r = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, true, g->st[1], b);
+            if (r) return r;
+            g->pf.bytes += b;
+        }
+        g->pf.rows[di] = rows;
+        any = any || !rows.empty();
+    }
+    OC_CUDA(cudaEventRecord(g->ev_pf, g->st[1]));
+    g->pf.active = true;
+    g->pf.sig = P.sig;
+    (void)any;
+    return OC_OK;
+}
+
+static int execute()
+{
+    if (g->queue.empty()) return OC_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<Loop> loops;
+    loops.swap(g->queue);
+    Plan* Pp = nullptr;
+    int rc = select_plan(loops, Pp);
+    if (rc) return rc;
+    Plan& P = *Pp;
+    g->last = Pp;
+
+    oc_stats_t& S = g->stats;
+    S.tiles = P.T;
+    S.tile_height = P.h;
+    S.depth = P.depth;
+    S.loops = P.L;
+    S.cell_updates = 0;
+    S.hbm_bytes = 0;
+    S.h2d_bytes = 0;
+    S.d2h_bytes = 0;
+    S.prefetched_bytes = 0;
+    S.graph_replays = 0;
+    S.kernel_launches = 0;
+    for (const Loop& lp : loops) {
+        double pts = (double)lp.points();
+        S.cell_updates += pts;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE)
+                S.hbm_bytes += pts * g->dats[ar.dat].esz * (ar.access == OC_RW ? 2 : 1);
+    }
+    if (g->dryrun) {
+        S.seconds = 0;
+        S.chains++;
+        return OC_OK;
+    }
+
+    auto dit = g->descs.find(P.sig);
+    if (dit == g->descs.end()) {
+        dit = g->descs.emplace(P.sig, std::vector<std::vector<LaunchDesc>>()).first;
+        build_descs(P, loops, dit->second);
+    }
+    const auto& tdesc = dit->second;
+    cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
+    rc = ensure_events(std::max(P.T, 1));
+    if (rc) return rc;
+
+    // parameters of every loop, one block
+    if ((size_t)P.nparams > g->h_params_cap) {
+        host_free(g->h_params, true);
+        g->h_params_cap = std::max<size_t>(P.nparams, 1024);
+        g->h_params = (double*)host_alloc(g->h_params_cap * 8, true);
+        if (!g->h_params) return fail(OC_ERR_NOMEM, "pinned parameter block");
+    }
+    if (g->h_results_cap < P.rp.size() || !g->h_results) {
+        host_free(g->h_results, true);
+        g->h_results_cap = std::max<size_t>(P.rp.size(), 64);
+        g->h_results = (double*)host_alloc(g->h_results_cap * 8, true);
+        if (!g->h_results) return fail(OC_ERR_NOMEM, "pinned result block");
+    }
+    for (int i = 0; i < P.L; ++i)
+        for (size_t j = 0; j < loops[i].params.size(); ++j) g->h_params[P.loop_param[i] + j] = loops[i].params[j];
+    const long long sb = scratch_base(P);
+
+    // a prefetch made for another plan must land before anything else touches slots
+    bool pf_match = g->pf.active && g->pf.sig == P.sig && !P.incore;
+    if (g->pf.active) {
+        for (int k = 0; k < 3; ++k) OC_CUDA(cudaStreamWaitEvent(g->st[k], g->ev_pf, 0));
+        if (!pf_match) g->pf.active = false;
+    }
+
+    if (P.nparams > 0)
+        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.params_off, g->h_params, (size_t)P.nparams * 8,
+                                cudaMemcpyHostToDevice, s0));
+
+    const bool use_graphs = (g->flags & OC_FLAG_GRAPHS) != 0;
+    GraphSet* gs = nullptr;
+    if (use_graphs) {
+        gs = &g->graphs[P.sig ^ ((g->flags & OC_FLAG_PROFILE) ? 0xABCDEFull : 0)];
+        if (gs->tiles.size() < (size_t)P.T) { gs->tiles.resize(P.T, nullptr); gs->prof.resize(P.T); }
+    }
+    auto run_compute = [&](int t) -> int {
+        if (use_graphs) {
+            if (!gs->tiles[t]) {
+                cudaGraph_t gr;
+                OC_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+                int r = run_tile_kernels(tdesc[t], s0, &gs->prof[t], true);
+                cudaError_t ce = cudaStreamEndCapture(s0, &gr);
+                if (r) return r;
+                if (ce != cudaSuccess) return fail(OC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+                OC_CUDA(cudaGraphInstantiate(&gs->tiles[t], gr, 0));
+                cudaGraphDestroy(gr);
+            } else {
+                S.graph_replays++;
+            }
+            OC_CUDA(cudaGraphLaunch(gs->tiles[t], s0));
+            for (const ProfRec& pr : gs->prof[t]) g->prof_pending.push_back(pr);
+        } else {
+            int r = run_tile_kernels(tdesc[t], s0);
+            if (r) return r;
+        }
+        S.kernel_launches += count_launches(tdesc[t]);
+        return OC_OK;
+    };
+
+    if (P.incore) {
+        // in-core: datasets stay resident; upload whatever is not on the device yet
+        bool up = false;
+        for (size_t di = 0; di < P.dp.size(); ++di) {
+            Dat& d = g->dats[P.dp[di].dat];
+            if (!d.dev_valid) {
+                OC_CUDA(cudaMemcpyAsync(g->arena + d.res_off, d.host, (size_t)d.bytes(), cudaMemcpyHostToDevice, s1));
+                S.h2d_bytes += (double)d.bytes();
+                d.dev_valid = true;
+                up = true;
+            }
+        }
+        if (up) {
+            OC_CUDA(cudaEventRecord(g->ev_up[0], s1));
+            OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[0], 0));
+        }
+        for (size_t di = 0; di < P.dp.size(); ++di) {
+            Dat& d = g->dats[P.dp[di].dat];
+            if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
+                rc = ghost_fill_device(d, s0);
+                if (rc) return rc;
+            }
+        }
+        if (P.T > 0) { rc = run_compute(0); if (rc) return rc; }
+        for (const Loop& lp : loops)
+            for (const Arg& ar : lp.args)
+                if (ar.access == OC_WRITE || ar.access == OC_RW) g->dats[ar.dat].host_valid = false;
+    } else {
+        for (size_t di = 0; di < P.dp.size(); ++di) {
+            const Dat& d = g->dats[P.dp[di].dat];
+            if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+        }
+        const int T = P.T, k = P.depth - 2;
+        for (int p = -k; p <= T; ++p) {
+            const int u = p + k;
+            if (u >= 0 && u < T) {
+                if (p - 1 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_comp[p - 1], 0));
+                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_down[p - 2], 0));
+                for (size_t di = 0; di < P.dp.size(); ++di) {
+                    const DatPlan& dp = P.dp[di];
+                    const Dat& d = g->dats[dp.dat];
+                    char* slab = g->arena + dp.off;
+                    const std::vector<Interval>* have = (u == 0 && pf_match) ? &g->pf.rows[di] : nullptr;
+                    for (const Interval& iv : dp.up) {
+                        if (iv.t != u) continue;
+                        rc = for_missing(iv, have, [&](int a, int b) {
+                            return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes);
+                        });
+                        if (rc) return rc;
+                    }
+                }
+                OC_CUDA(cudaEventRecord(g->ev_up[u], s1));
+            }
+            if (p >= 0 && p < T) {
+                OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
+                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
+                rc = run_compute(p);
+                if (rc) return rc;
+                OC_CUDA(cudaEventRecord(g->ev_comp[p], s0));
+            }
+            const int q = p - 1;
+            if (q >= 0 && q < T) {
+                OC_CUDA(cudaStreamWaitEvent(s2, g->ev_comp[q], 0));
+                for (size_t di = 0; di < P.dp.size(); ++di) {
+                    const DatPlan& dp = P.dp[di];
+                    const Dat& d = g->dats[dp.dat];
+                    for (const Interval& iv : dp.down)
+                        if (iv.t == q) {
+                            rc = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, false, s2, S.d2h_bytes);
+                            if (rc) return rc;
+                        }
+                }
+                OC_CUDA(cudaEventRecord(g->ev_down[q], s2));
+            }
+        }
+        if (pf_match) S.prefetched_bytes = g->pf.bytes;
+        g->pf.active = false;
+    }
+
+    // reductions: deterministic fold of the per-row partials
+    for (size_t r = 0; r < P.rp.size(); ++r) {
+        const RedPlan& rp = P.rp[r];
+        double* res = (double*)(g->arena + sb + P.results_off) + r;
+        cudaError_t e = launch_combine((const double*)(g->arena + sb + rp.part_off), rp.count, rp.op, res, s0);
+        if (e != cudaSuccess) return fail(OC_ERR_CUDA, "combine launch failed: %s", cudaGetErrorString(e));
+        S.kernel_launches++;
+    }
+    if (!P.rp.empty())
+        OC_CUDA(cudaMemcpyAsync(g->h_results, g->arena + sb + P.results_off, P.rp.size() * 8,
+                                cudaMemcpyDeviceToHost, s0));
+    if (!P.incore && (g->flags & OC_FLAG_PREFETCH)) {
+        rc = issue_prefetch(P);
+        if (rc) return rc;
+    }
+    rc = wait_stream(s0);
+    if (rc) return rc;
+    if (!P.incore && P.T > 0) {
+        rc = wait_event(g->ev_down[P.T - 1], g->timeout_s);
+        if (rc) return rc;
+    }
+    for (size_t r = 0; r < P.rp.size(); ++r) {
+        g->red_val[P.rp[r].handle] = g->h_results[r];
+        g->red_has[P.rp[r].handle] = 1;
+    }
+    if (!g->prof_pending.empty()) {
+        rc = collect_profile();
+        if (rc) return rc;
+    }
+    double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    S.seconds = sec;
+    S.total_seconds += sec;
+    S.total_cell_updates += S.cell_updates;
+    S.total_hbm_bytes += S.hbm_bytes;
+    S.total_h2d_bytes += S.h2d_bytes;
+    S.total_d2h_bytes += S.d2h_bytes;
+    S.chains++;
+    return OC_OK;
+}
+
+// ---------------------------------------------------------------------------------
+static bool known_kernel(int k) { return (k >= OC_K_COPY && k <= OC_K_HILO_ADD) || physics_kernel_known(k); }
+
+static int validate_loop(Loop& lp)
+{
+    const int nargs = (int)lp.args.size();
+    int ndim = -1, dtype = -1;
+    for (const Arg& ar : lp.args)
+        if (ar.access != OC_REDUCE) {
+            const Dat& d = g->dats[ar.dat];
+            if (ndim < 0) ndim = d.ndim;
+            if (d.ndim != ndim) return fail(OC_ERR_ARG, "loop mixes 2-D and 3-D datasets");
+            if (dtype < 0) dtype = d.dtype;
+            if (d.dtype != dtype) return fail(OC_ERR_ARG, "loop mixes element types");
+        }
+    if (ndim < 0) return fail(OC_ERR_ARG, "loop has no dataset argument");
+    lp.ndim = ndim;
+    const int sa = ndim - 1;
+    for (int a = ndim; a < 3; ++a) { lp.lo[a] = 0; lp.hi[a] = 1; }
+    for (Arg& ar : lp.args) {
+        if (ar.access == OC_REDUCE) continue;
+        const Dat& d = g->dats[ar.dat];
+        for (int a = 0; a < 3; ++a) { ar.rmin[a] = 0; ar.rmax[a] = 0; }
+        for (size_t p = 0; p < ar.off.size(); ++p)
+            for (int a = 0; a < 3; ++a) {
+                if (a >= ndim && ar.off[p][a] != 0) return fail(OC_ERR_ARG, "offset on a missing axis");
+                if (p == 0 || ar.off[p][a] < ar.rmin[a]) ar.rmin[a] = ar.off[p][a];
+                if (p == 0 || ar.off[p][a] > ar.rmax[a]) ar.rmax[a] = ar.off[p][a];
+            }
+        if (ar.access == OC_WRITE || ar.access == OC_RW) {
+            if (ar.off.size() != 1 || ar.off[0][0] || ar.off[0][1] || ar.off[0][2])
+                return fail(OC_ERR_ARG, "a written argument must use the single offset 0");
+        }
+        bool empty = false;
+        for (int a = 0; a < ndim; ++a) empty = empty || lp.lo[a] >= lp.hi[a];
+        if (empty) continue;
+        for (int a = 0; a < ndim; ++a) {
+            const bool wrap = (d.periodic & (1 << a)) && a != sa;
+            if (wrap) {
+                if (lp.lo[a] < 0 || lp.hi[a] > d.size[a] || ar.rmin[a] <= -d.size[a] || ar.rmax[a] >= d.size[a])
+                    return fail(OC_ERR_ARG, "periodic axis %d: range or offset out of [0, n)", a);
+            } else if (lp.lo[a] + ar.rmin[a] < -d.hlo[a] || lp.hi[a] - 1 + ar.rmax[a] >= d.size[a] + d.hhi[a]) {
+                return fail(OC_ERR_ARG, "argument on dataset %d reaches outside its allocated extent on axis %d", ar.dat, a);
+            }
+        }
+    }
+    // a dataset written by the loop may not be read at a non-zero offset
+    for (const Arg& w : lp.args) {
+        if (w.access != OC_WRITE && w.access != OC_RW) continue;
+        for (const Arg& r : lp.args) {
+            if (r.access != OC_READ || r.dat != w.dat) continue;
+            for (auto& o : r.off)
+                if (o[0] || o[1] || o[2]) return fail(OC_ERR_ARG, "dataset %d is written and read at a non-zero offset", w.dat);
+        }
+    }
+    auto acc = [&](int j) { return j < nargs ? lp.args[j].access : -1; };
+    auto npts = [&](int j) { return (int)lp.args[j].off.size(); };
+    switch (lp.kernel) {
+    case OC_K_COPY:
+        if (nargs != 2 || acc(0) != OC_WRITE || acc(1) != OC_READ || npts(1) != 1)
+            return fail(OC_ERR_ARG, "COPY takes [WRITE dst, READ src (1 point)]");
+        break;
+    case OC_K_LINCOMB: {
+        if (nargs < 2 || acc(0) != OC_WRITE) return fail(OC_ERR_ARG, "LINCOMB takes [WRITE dst, READ inputs...]");
+        int M = 0;
+        for (int j = 1; j < nargs; ++j) {
+            if (acc(j) != OC_READ) return fail(OC_ERR_ARG, "LINCOMB inputs must be READ");
+            M += npts(j);
+        }
+        if (M > kLaunchMaxSamples) return fail(OC_ERR_ARG, "LINCOMB supports at most %d samples", kLaunchMaxSamples);
+        if ((int)lp.params.size() != 1 + M) return fail(OC_ERR_ARG, "LINCOMB needs 1 + %d parameters", M);
+        break;
+    }
+    case OC_K_REDUCE:
+        if ((nargs != 2 && nargs != 3) || acc(nargs - 1) != OC_REDUCE || acc(0) != OC_READ ||
+            (nargs == 3 && acc(1) != OC_READ))
+            return fail(OC_ERR_ARG, "REDUCE takes [READ src0, (READ src1), REDUCE handle]");
+        for (int j = 0; j < nargs - 1; ++j)
+            if (npts(j) != 1 || lp.args[j].rmin[0] || lp.args[j].rmin[1] || lp.args[j].rmin[2] ||
+                lp.args[j].rmax[0] || lp.args[j].rmax[1] || lp.args[j].rmax[2])
+                return fail(OC_ERR_ARG, "REDUCE reads at offset 0 only");
+        if (lp.params.size() != 1) return fail(OC_ERR_ARG, "REDUCE needs [mode]");
+        break;
+    case OC_K_HILO_ADD:
+        if (nargs != 3 || acc(0) != OC_RW || acc(1) != OC_RW || acc(2) != OC_READ || npts(2) != 1 || dtype != OC_F32)
+            return fail(OC_ERR_ARG, "HILO_ADD takes [RW hi, RW lo, READ du] of F32 datasets");
+        if (lp.args[2].rmin[0] || lp.args[2].rmax[0] || lp.args[2].rmin[1] || lp.args[2].rmax[1] ||
+            lp.args[2].rmin[2] || lp.args[2].rmax[2])
+            return fail(OC_ERR_ARG, "HILO_ADD reads du at offset 0");
+        if (lp.params.size() != 1) return fail(OC_ERR_ARG, "HILO_ADD needs [scale]");
+        break;
+    default: {
+        std::string msg;
+        if (!physics_validate(lp, g->dats, msg)) return fail(OC_ERR_ARG, "%s", msg.c_str());
+    }
+    }
+    int reds = 0;
+    for (const Arg& ar : lp.args) reds += ar.access == OC_REDUCE;
+    if (reds > 1) return fail(OC_ERR_ARG, "at most one reduction argument per loop");
+    if (reds && lp.kernel != OC_K_REDUCE && !physics_kernel_reduces(lp.kernel))
+        return fail(OC_ERR_ARG, "kernel %d has no reduction argument", lp.kernel);
+    return OC_OK;
+}
+
+}  // namespace oc
+
+// =================================================================================
+using namespace oc;
+
+extern "C" {
+
+const char* oc_last_error(void) { return g_err; }
+
+int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[3], uint32_t flags,
+            int planner_mode)
+{
+    if (g) return fail(OC_ERR_STATE, "oc_init: context already exists");
+    if (budget == 0) return fail(OC_ERR_ARG, "oc_init: zero budget");
+    if (planner_mode < OC_PLAN_FIXED || planner_mode > OC_PLAN_LEARNED) return fail(OC_ERR_ARG, "oc_init: planner mode");
+    if (arena && arena_bytes < budget) return fail(OC_ERR_ARG, "oc_init: arena smaller than the budget");
+    if (!arena && arena_bytes != 0) return fail(OC_ERR_ARG, "oc_init: arena_bytes without an arena");
+    Ctx* c = new Ctx();
+    c->flags = flags;
+    c->planner_mode = planner_mode;
+    c->dryrun = (flags & OC_FLAG_DRYRUN) != 0;
+    c->budget = (long long)budget;
+    if (const char* t = getenv("OC_TIMEOUT_S")) c->timeout_s = atof(t);
+    g = c;
+    if (!c->dryrun) {
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || ndev == 0) {
+            delete c; g = nullptr;
+            return fail(OC_ERR_CUDA, "oc_init: no CUDA device (%s)", cudaGetErrorString(e));
+        }
+        if (arena) { c->arena = (char*)arena; c->arena_bytes = (long long)arena_bytes; }
+        else {
+            e = cudaMalloc((void**)&c->arena, budget);
+            if (e != cudaSuccess) { delete c; g = nullptr; return fail(OC_ERR_CUDA, "oc_init: arena allocation: %s", cudaGetErrorString(e)); }
+            c->own_arena = true;
+            c->arena_bytes = (long long)budget;
+        }
+        if (streams && streams[0] && streams[1] && streams[2]) {
+            for (int k = 0; k < 3; ++k) c->st[k] = (cudaStream_t)streams[k];
+        } else {
+            for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&c->st[k], cudaStreamNonBlocking);
+            c->own_streams = true;
+        }
+        cudaEventCreateWithFlags(&c->ev_pf, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming);
+    }
+    planner_reset();
+    return OC_OK;
+}
+
+int oc_finalize(void)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_finalize: no context");
+    if (!g->dryrun) {
+        for (int k = 0; k < 3; ++k) if (g->st[k]) cudaStreamSynchronize(g->st[k]);
+        for (auto& kv : g->graphs) {
+            for (auto ge : kv.second.tiles) if (ge) cudaGraphExecDestroy(ge);
+            for (auto& v : kv.second.prof) for (auto& pr : v) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
+        }
+        for (auto e : g->ev_pool) cudaEventDestroy(e);
+        for (auto e : g->ev_up) cudaEventDestroy(e);
+        for (auto e : g->ev_comp) cudaEventDestroy(e);
+        for (auto e : g->ev_down) cudaEventDestroy(e);
+        if (g->ev_pf) cudaEventDestroy(g->ev_pf);
+        if (g->ev_end) cudaEventDestroy(g->ev_end);
+        if (g->own_streams) for (int k = 0; k < 3; ++k) cudaStreamDestroy(g->st[k]);
+        if (g->own_arena) cudaFree(g->arena);
+    }
+    for (Dat& d : g->dats) host_free(d.host, d.host_pinned);
+    host_free(g->h_params, !g->dryrun);
+    host_free(g->h_results, !g->dryrun);
+    delete g;
+    g = nullptr;
+    planner_reset();
+    return OC_OK;
+}
+
+int oc_decl_dat(int ndim, const int size[3], const int halo_lo[3], const int halo_hi[3], int dtype,
+                const void* host_init, int periodic_mask, int* dat_out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_decl_dat: no context");
+    if (!dat_out || !size || !halo_lo || !halo_hi) return fail(OC_ERR_ARG, "oc_decl_dat: null pointer");
+    if (ndim != 2 && ndim != 3) return fail(OC_ERR_ARG, "oc_decl_dat: ndim must be 2 or 3");
+    if (dtype != OC_F64 && dtype != OC_F32) return fail(OC_ERR_ARG, "oc_decl_dat: dtype");
+    Dat d;
+    d.ndim = ndim;
+    for (int a = 0; a < ndim; ++a) {
+        if (size[a] < 1 || halo_lo[a] < 0 || halo_hi[a] < 0) return fail(OC_ERR_ARG, "oc_decl_dat: size/halo");
+        d.size[a] = size[a]; d.hlo[a] = halo_lo[a]; d.hhi[a] = halo_hi[a];
+        if ((periodic_mask & (1 << a)) && a != ndim - 1 && (halo_lo[a] || halo_hi[a]))
+            return fail(OC_ERR_ARG, "oc_decl_dat: a periodic fast axis has no halo");
+    }
+    d.dtype = dtype;
+    d.esz = dtype == OC_F64 ? 8 : 4;
+    d.periodic = periodic_mask & ((1 << ndim) - 1);
+    d.ox = (int)(align_up((long long)d.hlo[0] * d.esz, 16) / d.esz);
+    const long long line = d.ox + d.size[0] + d.hhi[0];
+    d.pitch = align_up(line, 128 / d.esz);
+    d.ylines = ndim == 3 ? d.ext(1) : 1;
+    d.row_elems = d.pitch * d.ylines;
+    d.nrows = d.ext(ndim - 1);
+    d.y0 = -d.hlo[ndim - 1];
+    if (!g->dryrun) {
+        d.host = host_alloc((size_t)d.bytes(), true);
+        if (!d.host) return fail(OC_ERR_NOMEM, "oc_decl_dat: pinned allocation of %lld bytes failed", d.bytes());
+        d.host_pinned = true;
+        memset(d.host, 0, (size_t)d.bytes());
+        if (host_init) {
+            const long long ext0 = d.ext(0);
+            const char* src = (const char*)host_init;
+            char* dst = (char*)d.host;
+            for (long long r = 0; r < d.nrows; ++r)
+                for (long long l = 0; l < d.ylines; ++l)
+                    memcpy(dst + ((r * d.row_elems) + l * d.pitch + d.ox - d.hlo[0]) * d.esz,
+                           src + ((r * d.ylines + l) * ext0) * d.esz, (size_t)(ext0 * d.esz));
+        }
+    }
+    d.host_valid = true;
+    g->dats.push_back(d);
+    *dat_out = (int)g->dats.size() - 1;
+    return OC_OK;
+}
+
+int oc_decl_reduction(int op, int* red_out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_decl_reduction: no context");
+    if (!red_out || op < OC_SUM || op > OC_MIN) return fail(OC_ERR_ARG, "oc_decl_reduction: op");
+    g->red_ops.push_back(op);
+    g->red_val.push_back(0.0);
+    g->red_has.push_back(0);
+    *red_out = (int)g->red_ops.size() - 1;
+    return OC_OK;
+}
+
+int oc_enqueue_loop(int kernel_id, const int range_lo[3], const int range_hi[3], int nargs,
+                    const oc_arg* args, const double* params, int nparams)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_enqueue_loop: no context");
+    if (!known_kernel(kernel_id)) return fail(OC_ERR_ARG, "unknown kernel id %d", kernel_id);
+    if (nargs < 1 || nargs > kMaxArgs || !args || !range_lo || !range_hi) return fail(OC_ERR_ARG, "oc_enqueue_loop: arguments");
+    if (nparams < 0 || (nparams > 0 && !params)) return fail(OC_ERR_ARG, "oc_enqueue_loop: parameters");
+    Loop lp;
+    lp.kernel = kernel_id;
+    for (int a = 0; a < 3; ++a) { lp.lo[a] = range_lo[a]; lp.hi[a] = range_hi[a]; }
+    int ndim = 0;
+    for (int j = 0; j < nargs; ++j) {
+        const oc_arg& a = args[j];
+        Arg ar;
+        ar.dat = a.dat;
+        ar.access = a.access;
+        if (a.access == OC_REDUCE) {
+            if (a.dat < 0 || a.dat >= (int)g->red_ops.size()) return fail(OC_ERR_ARG, "bad reduction handle %d", a.dat);
+        } else {
+            if (a.access != OC_READ && a.access != OC_WRITE && a.access != OC_RW) return fail(OC_ERR_ARG, "bad access mode %d", a.access);
+            if (a.dat < 0 || a.dat >= (int)g->dats.size()) return fail(OC_ERR_ARG, "bad dataset handle %d", a.dat);
+            ndim = g->dats[a.dat].ndim;
+            if (a.npoints < 1 || a.npoints > kLaunchMaxSamples || !a.offsets) return fail(OC_ERR_ARG, "bad stencil");
+            for (int p = 0; p < a.npoints; ++p) {
+                std::array<int, 3> o = {0, 0, 0};
+                for (int q = 0; q < ndim; ++q) o[q] = a.offsets[p * ndim + q];
+                ar.off.push_back(o);
+            }
+        }
+        lp.args.push_back(ar);
+    }
+    for (int i = 0; i < nparams; ++i) lp.params.push_back(params[i]);
+    int r = validate_loop(lp);
+    if (r) return r;
+    g->queue.push_back(std::move(lp));
+    return OC_OK;
+}
+
+int oc_flush(void)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_flush: no context");
+    return execute();
+}
+
+int oc_reduce(int red, double* out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_reduce: no context");
+    if (red < 0 || red >= (int)g->red_ops.size() || !out) return fail(OC_ERR_ARG, "oc_reduce: handle");
+    int r = execute();
+    if (r) return r;
+    if (g->dryrun) return fail(OC_ERR_STATE, "oc_reduce: dry-run context executes nothing");
+    if (!g->red_has[red]) return fail(OC_ERR_STATE, "oc_reduce: reduction %d was never computed", red);
+    *out = g->red_val[red];
+    return OC_OK;
+}
+
+int oc_fetch_dat(int dat, void* host_out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_fetch_dat: no context");
+    if (dat < 0 || dat >= (int)g->dats.size() || !host_out) return fail(OC_ERR_ARG, "oc_fetch_dat: handle");
+    int r = execute();
+    if (r) return r;
+    if (g->dryrun) return fail(OC_ERR_STATE, "oc_fetch_dat: dry-run context holds no data");
+    Dat& d = g->dats[dat];
+    if (d.resident && !d.host_valid) {
+        OC_CUDA(cudaMemcpyAsync(d.host, g->arena + d.res_off, (size_t)d.bytes(), cudaMemcpyDeviceToHost, g->st[2]));
+        r = wait_stream(g->st[2]);
+        if (r) return r;
+        d.host_valid = true;
+    }
+    const long long ext0 = d.ext(0);
+    char* dst = (char*)host_out;
+    const char* src = (const char*)d.host;
+    for (long long row = 0; row < d.nrows; ++row)
+        for (long long l = 0; l < d.ylines; ++l)
+            memcpy(dst + ((row * d.ylines + l) * ext0) * d.esz,
+                   src + ((row * d.row_elems) + l * d.pitch + d.ox - d.hlo[0]) * d.esz, (size_t)(ext0 * d.esz));
+    return OC_OK;
+}
+
+int oc_set_flag(uint32_t flag, int on)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_set_flag: no context");
+    if (flag & ~(OC_FLAG_CYCLIC | OC_FLAG_PREFETCH | OC_FLAG_GRAPHS | OC_FLAG_PROFILE))
+        return fail(OC_ERR_ARG, "oc_set_flag: flag");
+    if (on) g->flags |= flag;
+    else g->flags &= ~flag;
+    return OC_OK;
+}
+
+int oc_set_tiling(int tile_height, int depth)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_set_tiling: no context");
+    if (tile_height < 0 || depth < 0 || depth == 1 || depth > 4) return fail(OC_ERR_ARG, "oc_set_tiling: values");
+    g->force_h = tile_height;
+    g->force_depth = depth;
+    return OC_OK;
+}
+
+int oc_stats(oc_stats_t* out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_stats: no context");
+    if (!out) return fail(OC_ERR_ARG, "oc_stats: null");
+    *out = g->stats;
+    return OC_OK;
+}
+
+int oc_kernel_stats(int kernel_id, oc_kernel_stats_t* out)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_kernel_stats: no context");
+    if (!out) return fail(OC_ERR_ARG, "oc_kernel_stats: null");
+    auto it = g->kstats.find(kernel_id);
+    KStat k = it == g->kstats.end() ? KStat() : it->second;
+    out->launches = k.launches;
+    out->ms = k.ms;
+    out->bytes = k.bytes;
+    out->points = k.points;
+    return OC_OK;
+}
+
+int oc_kernel_stats_reset(void)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_kernel_stats_reset: no context");
+    g->kstats.clear();
+    return OC_OK;
+}
+
+int oc_plan_shape(int* ntiles, int* nloops, int* ndats, int* tile_height, int* depth, int* slow_rows)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_plan_shape: no context");
+    static const Plan empty;
+    const Plan& P = g->last ? *g->last : empty;
+    if (ntiles) *ntiles = P.T;
+    if (nloops) *nloops = P.L;
+    if (ndats) *ndats = (int)P.dp.size();
+    if (tile_height) *tile_height = P.h;
+    if (depth) *depth = P.depth;
+    if (slow_rows) *slow_rows = P.Y1 - P.Y0;
+    return OC_OK;
+}
+
+int oc_plan_ranges(int* se)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_plan_ranges: no context");
+    if (!se) return fail(OC_ERR_ARG, "oc_plan_ranges: null");
+    if (g->last) std::copy(g->last->se.begin(), g->last->se.end(), se);
+    return OC_OK;
+}
+
+int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup, int* down, int cap_down,
+                int* ndown)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_plan_dat: no context");
+    if (!g->last) return fail(OC_ERR_STATE, "oc_plan_dat: no plan yet");
+    const Plan& P = *g->last;
+    if (k < 0 || k >= (int)P.dp.size()) return fail(OC_ERR_ARG, "oc_plan_dat: index");
+    const DatPlan& dp = P.dp[k];
+    if (dat) *dat = dp.dat;
+    if (slab_rows) *slab_rows = dp.S;
+    if (nup) *nup = (int)dp.up.size();
+    if (ndown) *ndown = (int)dp.down.size();
+    if ((int)dp.up.size() > cap_up || (int)dp.down.size() > cap_down)
+        return fail(OC_ERR_ARG, "oc_plan_dat: capacity too small");
+    for (size_t j = 0; j < dp.up.size(); ++j) { up[3 * j] = dp.up[j].t; up[3 * j + 1] = dp.up[j].a; up[3 * j + 2] = dp.up[j].b; }
+    for (size_t j = 0; j < dp.down.size(); ++j) { down[3 * j] = dp.down[j].t; down[3 * j + 1] = dp.down[j].a; down[3 * j + 2] = dp.down[j].b; }
+    return OC_OK;
+}
+
+}  // extern "C"

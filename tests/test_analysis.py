@@ -1,0 +1,182 @@
+"""Host-only tests of the chain analysis inside liboc.so (dry-run contexts, no GPU).
+
+The skew analysis, footprints, copy sets and slab sizes (arXiv 1709.02125, Sec. 3 and
+Sec. 4 / Algorithm 1 / Sec. 4.1) are checked by a brute-force legality checker and by
+replaying each plan on tagged CPU slabs with the oracle's kernels.
+"""
+import numpy as np
+import pytest
+
+from workloads import heat, random_chain
+from workloads.spec import READ, REDUCE, WRITE, Arg, DatSpec, Loop, RedSpec
+
+import plan_sim
+
+oc = pytest.importorskip("paper_1709_02125_gb300.oc")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build_lib()
+    return oc.load()
+
+
+def dry(budget, dats, reds, loops, h=0, depth=0, flags=0):
+    with oc.Executor(budget, dryrun=True, flags=flags) as ex:
+        ex.set_tiling(h, depth)
+        oc.run_chain(ex, dats, reds, loops)
+        return ex.plan(), ex.stats(), dict(ex.names)
+
+
+def random3d(n=12, nz=20, nfields=6, nloops=10, seed=0):
+    rng = np.random.default_rng(seed)
+    loops = []
+    for _ in range(nloops):
+        w = int(rng.integers(0, nfields))
+        ins = rng.choice([f for f in range(nfields) if f != w], size=int(rng.integers(1, 3)), replace=False)
+        args = [Arg(f"g{w}", WRITE)]
+        for f in ins:
+            pts = [tuple(int(v) for v in rng.integers(-1, 2, size=3)) for _ in range(int(rng.integers(1, 4)))]
+            args.append(Arg(f"g{int(f)}", READ, sorted(set(pts))))
+        m = sum(len(a.offsets) for a in args[1:])
+        c = rng.uniform(-1, 1, size=m)
+        c *= 0.5 / np.abs(c).sum()
+        loops.append(Loop("lincomb", (0, 0, 0), (n, n, nz), args, [0.5] + list(c)))
+    dats = [DatSpec(f"g{f}", (n, n, nz), (1, 1, 1), (1, 1, 1),
+                    init=rng.uniform(-1, 1, size=(nz + 2, n + 2, n + 2))) for f in range(nfields)]
+    reds = [RedSpec("s", "sum")]
+    loops.append(Loop("reduce", (0, 0, 0), (n, n, nz), [Arg("g0", READ), Arg("s", REDUCE)], [0.0]))
+    return dats, reds, loops
+
+
+def test_heat_four_tiles_under_one_mib(lib):
+    dats, reds, loops = heat.build(256, 10)
+    plan, st, _ = dry(1 << 20, dats, reds, loops, h=64, depth=3)
+    assert plan["tiles"] == 4
+    plan_sim.check_legality(plan, loops)
+    # 10 steps of (A, B): the first loop runs ahead of the last one by 2 rows per step
+    r = plan["ranges"]
+    assert r[0, 0, 1] - r[0, -1, 1] <= 21
+    assert st["cell_updates"] == 30 * 256 * 256
+
+
+def test_heat_too_small_budget_is_rejected(lib):
+    dats, reds, loops = heat.build(256, 10)
+    with pytest.raises(oc.OcError) as e:
+        dry(64 << 10, dats, reds, loops)
+    assert e.value.code == oc.OC_ERR_BUDGET
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("h,depth", [(1, 3), (3, 2), (5, 3), (7, 4)])
+def test_random_chain_plans_are_legal(lib, seed, h, depth):
+    dats, reds, loops = random_chain.build(n=40, nfields=10, nloops=24, seed=100 + seed, with_init=False)
+    plan, _, _ = dry(1 << 30, dats, reds, loops, h=h, depth=depth)
+    assert plan["tiles"] == -(-40 // h)
+    plan_sim.check_legality(plan, loops)
+
+
+@pytest.mark.parametrize("seed,h,depth", [(0, 3, 3), (1, 4, 2), (2, 6, 4), (3, 2, 3)])
+def test_random_chain_simulation_matches_oracle(lib, oracle_lib, seed, h, depth):
+    dats, reds, loops = random_chain.build(n=24, nfields=8, nloops=16, seed=200 + seed)
+    plan, _, names = dry(1 << 30, dats, reds, loops, h=h, depth=depth)
+    plan_sim.check_legality(plan, loops)
+    got, gred = plan_sim.simulate(plan, loops, dats, reds, oracle_lib, names)
+    ref = oracle_lib.make_fields(dats)
+    rred = oracle_lib.run_chain(loops, ref, reds)
+    for d in dats:
+        assert np.array_equal(got[d.name].a, ref[d.name].a), d.name
+    for r in reds:
+        assert abs(gred[r.name] - rred[r.name]) <= 1e-12 * max(1.0, abs(rred[r.name]))
+
+
+@pytest.mark.parametrize("h,depth", [(2, 3), (5, 2), (3, 4)])
+def test_random_3d_simulation_matches_oracle(lib, oracle_lib, h, depth):
+    dats, reds, loops = random3d(seed=h)
+    plan, _, names = dry(1 << 30, dats, reds, loops, h=h, depth=depth)
+    plan_sim.check_legality(plan, loops)
+    got, _ = plan_sim.simulate(plan, loops, dats, reds, oracle_lib, names)
+    ref = oracle_lib.make_fields(dats)
+    oracle_lib.run_chain(loops, ref, reds)
+    for d in dats:
+        assert np.array_equal(got[d.name].a, ref[d.name].a), d.name
+
+
+def test_heat_simulation_bit_exact(lib, oracle_lib):
+    dats, reds, loops = heat.build(64, 10)
+    plan, _, names = dry(1 << 30, dats, reds, loops, h=16, depth=3)
+    got, gred = plan_sim.simulate(plan, loops, dats, reds, oracle_lib, names)
+    ref = oracle_lib.make_fields(dats)
+    rred = oracle_lib.run_chain(loops, ref, reds)
+    assert np.array_equal(got["u"].a, ref["u"].a)
+    assert all(gred[k] == rred[k] for k in rred)
+
+
+def test_budget_fit_is_largest_height(lib):
+    dats, reds, loops = random_chain.build(n=64, nfields=8, nloops=12, seed=5, with_init=False)
+    fp = random_chain.footprint_bytes(64, 8)
+    plan, _, _ = dry(fp // 3, dats, reds, loops)
+    h = plan["tile_height"]
+    assert 1 <= h < 64
+    plan_sim.check_legality(plan, loops)
+    # one more row per tile no longer fits (the fixed rule picks the largest fitting height)
+    with pytest.raises(oc.OcError) as e:
+        dry(fp // 3, dats, reds, loops, h=h + 1, depth=3)
+    assert e.value.code == oc.OC_ERR_BUDGET
+
+
+def test_write_first_and_read_only_copies(lib):
+    """Sec. 4.1: a dataset first written over whole rows is never uploaded, a dataset
+    only read is never downloaded; with the cyclic flag the write-first one is not
+    downloaded either."""
+    n = 32
+    dats = [DatSpec("a", (n, n), (1, 1), (1, 1)), DatSpec("t", (n, n), (0, 1), (0, 1)),
+            DatSpec("b", (n, n), (1, 1), (1, 1))]
+    loops = [Loop("copy", (0, 0), (n, n), [Arg("t", WRITE), Arg("a", READ, [(0, 1)])]),
+             Loop("lincomb", (0, 0), (n, n), [Arg("b", WRITE), Arg("t", READ, [(0, 0), (0, -1)])], [0.0, 0.5, 0.5])]
+    for flags, t_down in ((0, True), (oc.OC_FLAG_CYCLIC, False)):
+        plan, _, names = dry(1 << 30, dats, [], loops, h=8, depth=3, flags=flags)
+        by = {d["dat"]: d for d in plan["dats"]}
+        a, t, b = by[names["a"]], by[names["t"]], by[names["b"]]
+        assert len(a["up"]) > 0 and len(a["down"]) == 0          # read-only: never downloaded
+        up_rows = {y for _, lo, hi in t["up"] for y in range(lo, hi)}
+        assert up_rows <= {-1, n}                                 # only halo rows it reads unwritten
+        assert (len(t["down"]) > 0) == t_down
+        assert len(b["up"]) > 0                                   # partial-row write keeps the halo
+
+
+@pytest.mark.parametrize("bad", ["write_offset", "extent", "self_read", "lincomb_params", "mixed_dtype"])
+def test_invalid_loops_rejected(lib, bad):
+    n = 8
+    with oc.Executor(1 << 20, dryrun=True) as ex:
+        _bad(ex, n, bad)
+
+
+def _bad(ex, n, bad):
+    for d in [DatSpec("a", (n, n), (1, 1), (1, 1)), DatSpec("b", (n, n), (1, 1), (1, 1)),
+              DatSpec("c", (n, n), (1, 1), (1, 1), dtype="f32")]:
+        ex.decl_dat(d)
+    lp = {
+        "write_offset": Loop("copy", (0, 0), (n, n), [Arg("b", WRITE, [(1, 0)]), Arg("a", READ)]),
+        "extent": Loop("copy", (0, 0), (n, n), [Arg("b", WRITE), Arg("a", READ, [(2, 0)])]),
+        "self_read": Loop("lincomb", (0, 0), (n, n), [Arg("b", WRITE), Arg("b", READ, [(0, 1)])], [0.0, 1.0]),
+        "lincomb_params": Loop("lincomb", (0, 0), (n, n), [Arg("b", WRITE), Arg("a", READ, [(0, 1)])], [0.0]),
+        "mixed_dtype": Loop("copy", (0, 0), (n, n), [Arg("c", WRITE), Arg("a", READ)]),
+    }[bad]
+    with pytest.raises(oc.OcError) as e:
+        ex.enqueue(lp)
+    assert e.value.code == oc.OC_ERR_ARG
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import re
+    import os
+    hdr = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+    names = set()
+    for f in os.listdir(hdr):
+        if f.endswith(".h"):
+            names |= set(re.findall(r"^\s*(?:int|const char\*|void)\s+\**(oc_\w+)\s*\(", open(os.path.join(hdr, f)).read(), re.M))
+    assert names, "no declarations found"
+    for n in sorted(names):
+        assert hasattr(lib, n), n
