@@ -79,12 +79,15 @@ extern "C" {
  *                  be inspected with oc_plan_*), nothing is executed, and
  *                  oc_reduce / oc_fetch_dat return OC_ERR_STATE. Host-only use.
  * OC_FLAG_PROFILE  bracket every kernel launch with CUDA events on the compute
- *                  stream and accumulate per-kernel device time (oc_kernel_stats). */
+ *                  stream and accumulate per-kernel device time (oc_kernel_stats).
+ * OC_FLAG_TRACE    record the device time line of every tile's upload, compute and
+ *                  download of the last flush (oc_trace). */
 #define OC_FLAG_CYCLIC   0x1u
 #define OC_FLAG_PREFETCH 0x2u
 #define OC_FLAG_GRAPHS   0x4u
 #define OC_FLAG_DRYRUN   0x8u
 #define OC_FLAG_PROFILE  0x10u
+#define OC_FLAG_TRACE    0x20u
 
 /* ---- planner modes ----------------------------------------------------------
  * OC_PLAN_FIXED     largest tile height whose plan fits the budget, depth 3.
@@ -99,18 +102,21 @@ extern "C" {
 /* ---- loop kernels (kernel_id of oc_enqueue_loop) ------------------------------
  * Every kernel is a pointwise function of its READ arguments sampled at their
  * stencil offsets; WRITE/RW arguments are accessed at offset 0 only. For every
- * point the result is evaluated in exactly the order written below (IEEE
- * round-to-nearest, no fused multiply-add), so that any two correct
- * implementations agree bit for bit on FP64 data.
+ * point the result is evaluated in the order written below (IEEE round-to-nearest;
+ * a multiply-add is fused only where stated), so two correct implementations differ
+ * by at most the rounding of the fused steps; tiled and untiled executions of this
+ * library agree bit for bit.
  *
  * OC_K_COPY     args: [0] WRITE dst (1 point, offset 0), [1] READ src (1 point).
  *               dst(p) = src(p + o).                               params: none.
  * OC_K_LINCOMB  args: [0] WRITE dst; [1..k] READ inputs, input j with n_j points.
  *               Let x_0..x_{M-1} be the samples in argument order, then point
  *               order (M = sum n_j). params = [alpha, c_0, ..., c_{M-1}].
- *               acc = c_0*x_0; acc = acc + c_m*x_m for m = 1..M-1; if alpha != 0:
+ *               acc = c_0*x_0; acc = c_m*x_m + acc for m = 1..M-1 (this multiply-add
+ *               may be fused: one rounding); if alpha != 0:
  *               acc = acc + ((alpha*a)*b) / (1 + c*c) with a = x_0,
- *               b = x_{1 mod M}, c = x_{2 mod M}. dst(p) = acc.
+ *               b = x_{1 mod M}, c = x_{2 mod M}. dst(p) = acc. FP32 datasets use
+ *               the parameters rounded to float.
  * OC_K_REDUCE   args: [0] READ src0 (offset 0), optionally [1] READ src1 (offset 0),
  *               last: REDUCE handle. v = src0(p) (+ src1(p)), converted to double
  *               before the addition; params = [mode]: 0 -> v, 1 -> |v|, 2 -> v*v.
@@ -234,6 +240,19 @@ typedef struct oc_kernel_stats_t {
 } oc_kernel_stats_t;
 int oc_kernel_stats(int kernel_id, oc_kernel_stats_t* out);
 int oc_kernel_stats_reset(void);
+
+/* Time line of the last flush under OC_FLAG_TRACE: one record per tile and phase kind
+ * (0 upload on stream 1, 1 compute on stream 0, 2 download on stream 2), with device
+ * times in ms relative to the start of the flush and the bytes moved (uploads and
+ * downloads). *n receives the number of records; at most cap are written. */
+typedef struct oc_trace_rec {
+    int tile;
+    int kind;
+    double start_ms;
+    double end_ms;
+    double bytes;
+} oc_trace_rec;
+int oc_trace(oc_trace_rec* out, int cap, int* n);
 
 /* Message of the last error (static storage, valid until the next call). */
 const char* oc_last_error(void);

@@ -294,6 +294,8 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
     P.nparams = np;
     P.params_off = off;
     off += align_up(std::max(1, np) * 8, 256);
+    P.paramsf_off = off;
+    off += align_up(std::max(1, np) * 4, 256);
     P.results_off = off;
     off += align_up(std::max<long long>(1, (long long)P.rp.size()) * 8, 256);
     P.scratch_bytes = off;

@@ -8,9 +8,10 @@
 // modulo. x is the fastest axis, so a warp reads 32 consecutive elements of one
 // x-line (coalesced); rows of neighbouring samples are shared through L1/L2.
 //
-// Arithmetic follows the evaluation order stated in include/oc.h for every point;
-// the library is compiled with -fmad=false so no multiply-add is contracted and the
-// FP64 results are bit-identical to any IEEE implementation of the same order.
+// Arithmetic follows the evaluation order stated in include/oc.h for every point.
+// The library is compiled with -fmad=false, so the only fused multiply-adds are the
+// explicit ones (__fma_rn) that the stated order allows; a tiled and an untiled run
+// execute the same instructions per point and agree bit for bit.
 #include <cuda_runtime.h>
 
 #include "../../include/oc.h"
@@ -40,7 +41,49 @@ __device__ __forceinline__ int first_slot(const DView& v, int s)
     return slot >= v.S ? slot - v.S : slot;
 }
 
+template <typename T>
+__device__ __forceinline__ const T* params_of(const LaunchDesc& d);
+template <>
+__device__ __forceinline__ const float* params_of<float>(const LaunchDesc& d) { return d.paramsf; }
+template <>
+__device__ __forceinline__ const double* params_of<double>(const LaunchDesc& d) { return d.params; }
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One stencil sample m for the R rows of this thread: load, then accumulate.
 template <typename T, int R>
+__device__ __forceinline__ void lincomb_sample(const LaunchDesc& d, const T* cp, int m, int x, int yl,
+                                               int s0, int shi, T (&acc)[R], T (&x0)[R], T (&x1)[R],
+                                               T (&x2)[R])
+{
+    const int sa = d.ndim - 1;
+    const DView& v = d.v[d.sarg[m]];
+    const T c = cp[1 + m];
+    const T* col = col_ptr<T>(v, x + d.soff[m][0], yl + (d.ndim == 3 ? d.soff[m][1] : 0));
+    int slot = first_slot(v, s0 + d.soff[m][sa]);
+    T val[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        val[r] = T(0);
+        if (s0 + r < shi) val[r] = __ldg(col + (long long)slot * v.row_elems);
+        if (++slot == v.S) slot = 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (m == 0) { acc[r] = c * val[r]; x0[r] = val[r]; }
+        else {
+            acc[r] = fma_t(c, val[r], acc[r]);
+            if (m == 1) x1[r] = val[r];
+            if (m == 2) x2[r] = val[r];
+        }
+    }
+}
+
+// LINCOMB (include/oc.h): acc = c0 x0, acc = c_m x_m + acc (fused), then the bounded
+// nonlinear term. M > 0: the sample count is a compile-time constant, so the loop is
+// fully unrolled and all R*M loads of a thread are independent; M == 0: any count.
+template <typename T, int R, int M>
 __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ LaunchDesc d)
 {
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
@@ -49,37 +92,26 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ L
     const int yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
     const int s0 = d.lo[sa] + (int)blockIdx.z * R;
     const int shi = d.hi[sa];
-    const int M = d.nsamp;
+    const int nM = M > 0 ? M : d.nsamp;
+    const T* cp = params_of<T>(d);
 
     T acc[R], x0[R], x1[R], x2[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc[r] = T(0); x0[r] = x1[r] = x2[r] = T(0); }
-
-    for (int m = 0; m < M; ++m) {
-        const DView& v = d.v[d.sarg[m]];
-        const T c = (T)d.params[1 + m];
-        const T* col = col_ptr<T>(v, x + d.soff[m][0], yl + (d.ndim == 3 ? d.soff[m][1] : 0));
-        int slot = first_slot(v, s0 + d.soff[m][sa]);
+    if (M > 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            T val = T(0);
-            if (s0 + r < shi) val = __ldg(col + (long long)slot * v.row_elems);
-            if (++slot == v.S) slot = 0;
-            if (m == 0) { acc[r] = c * val; x0[r] = val; }
-            else {
-                acc[r] = acc[r] + c * val;
-                if (m == 1) x1[r] = val;
-                if (m == 2) x2[r] = val;
-            }
-        }
+        for (int m = 0; m < M; ++m) lincomb_sample<T, R>(d, cp, m, x, yl, s0, shi, acc, x0, x1, x2);
+    } else {
+#pragma unroll 1
+        for (int m = 0; m < nM; ++m) lincomb_sample<T, R>(d, cp, m, x, yl, s0, shi, acc, x0, x1, x2);
     }
-    const T alpha = (T)d.params[0];
+    const T alpha = cp[0];
     if (alpha != T(0)) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const T a = x0[r];
-            const T b = M > 1 ? x1[r] : x0[r];
-            const T c = M > 2 ? x2[r] : x0[r];
+            const T b = nM > 1 ? x1[r] : x0[r];
+            const T c = nM > 2 ? x2[r] : x0[r];
             acc[r] = acc[r] + ((alpha * a) * b) / (T(1) + c * c);
         }
     }
@@ -132,7 +164,7 @@ __global__ void __launch_bounds__(kThreadsX) k_hilo_add(const __grid_constant__ 
     const int yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
     const int s0 = d.lo[sa] + (int)blockIdx.z * R;
     const int shi = d.hi[sa];
-    const float scale = (float)d.params[0];
+    const float scale = d.paramsf[0];
     float* hp = const_cast<float*>(col_ptr<float>(d.v[0], x, yl));
     float* lp = const_cast<float*>(col_ptr<float>(d.v[1], x, yl));
     const float* up = col_ptr<float>(d.v[2], x, yl);
@@ -249,6 +281,25 @@ cudaError_t launch_pointwise(const LaunchDesc& d, cudaStream_t st, F kern)
     return cudaGetLastError();
 }
 
+template <typename T, int M>
+cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
+{
+    return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
+}
+
+// Dispatch on the number of samples: 1..20 get a fully unrolled instance.
+template <typename T>
+cudaError_t launch_lincomb(const LaunchDesc& d, cudaStream_t st)
+{
+    switch (d.nsamp) {
+#define OC_LC(M) case M: return lincomb_m<T, M>(d, st);
+        OC_LC(1) OC_LC(2) OC_LC(3) OC_LC(4) OC_LC(5) OC_LC(6) OC_LC(7) OC_LC(8) OC_LC(9) OC_LC(10)
+        OC_LC(11) OC_LC(12) OC_LC(13) OC_LC(14) OC_LC(15) OC_LC(16) OC_LC(17) OC_LC(18) OC_LC(19) OC_LC(20)
+#undef OC_LC
+    default: return lincomb_m<T, 0>(d, st);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
@@ -258,7 +309,7 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
     case OC_K_COPY:
         return f32 ? launch_pointwise(d, st, k_copy<float, kRows>) : launch_pointwise(d, st, k_copy<double, kRows>);
     case OC_K_LINCOMB:
-        return f32 ? launch_pointwise(d, st, k_lincomb<float, kRows>) : launch_pointwise(d, st, k_lincomb<double, kRows>);
+        return f32 ? launch_lincomb<float>(d, st) : launch_lincomb<double>(d, st);
     case OC_K_HILO_ADD:
         return launch_pointwise(d, st, k_hilo_add<kRows>);
     case OC_K_REDUCE: {

@@ -7,7 +7,7 @@
 
 namespace oc {
 
-constexpr int kLaunchMaxArgs = 24;
+constexpr int kLaunchMaxArgs = 32;
 constexpr int kLaunchMaxSamples = 64;
 
 // Device view of one dataset argument inside one launch. A slow row s lives at
@@ -39,6 +39,7 @@ struct LaunchDesc {
     int sarg[kLaunchMaxSamples];
     int soff[kLaunchMaxSamples][3];
     const double* params;      // device pointer to this loop's parameters
+    const float* paramsf;      // the same parameters rounded to float (FP32 kernels)
     int nparams;
     double* part;              // reduction partials of this loop (row part_row0 first)
     int part_row0;

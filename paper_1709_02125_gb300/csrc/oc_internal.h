@@ -10,7 +10,7 @@
 
 namespace oc {
 
-constexpr int kMaxArgs = 24;
+constexpr int kMaxArgs = 32;
 constexpr int kMaxSamples = 64;
 
 // A dataset (arXiv 1709.02125, Sec. 3) with the library-owned host store.
@@ -102,7 +102,7 @@ struct Plan {
     std::vector<int> loop_red;           // per loop: index into rp (or -1)
     std::vector<int> loop_param;         // per loop: offset (doubles) into the parameter block
     int nparams = 0;
-    long long params_off = 0, results_off = 0;
+    long long params_off = 0, paramsf_off = 0, results_off = 0;
     long long slab_bytes = 0;            // bytes of all slabs
     long long scratch_bytes = 0;         // partials + parameters + results
     long long arena_bytes = 0;           // slab_bytes + scratch_bytes

@@ -118,6 +118,13 @@ struct Ctx {
     size_t ev_next = 0;
     std::vector<ProfRec> prof_pending;
     std::unordered_map<int, KStat> kstats;
+    // tracing (OC_FLAG_TRACE)
+    struct TraceRec { int tile, kind; cudaEvent_t a, b; double bytes; };
+    std::vector<cudaEvent_t> tr_pool;
+    size_t tr_next = 0;
+    std::vector<TraceRec> tr;
+    cudaEvent_t tr_t0 = nullptr;
+    std::vector<oc_trace_rec> tr_out;
 };
 
 static Ctx* g = nullptr;
@@ -289,6 +296,7 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
             if (lp.kernel == OC_K_REDUCE) ns = 0;
             d.nsamp = ns;
             d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
+            d.paramsf = (const float*)(g->arena + sb + P.paramsf_off) + P.loop_param[i];
             d.nparams = (int)lp.params.size();
             if (P.loop_red[i] >= 0) {
                 d.part = (double*)(g->arena + sb + P.loop_part[i]);
@@ -334,16 +342,61 @@ static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
             if (r) return r;
             pr.kernel = d.kernel;
             pr.bytes = launch_bytes(d, pr.points);
-            OC_CUDA(cudaEventRecord(pr.a, s));
+            // inside a stream capture only an "external" record becomes a graph node
+            OC_CUDA(cudaEventRecordWithFlags(pr.a, s, persistent ? cudaEventRecordExternal : cudaEventRecordDefault));
         }
         cudaError_t e = launch_loop(d, s);
         if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", d.kernel, cudaGetErrorString(e));
         if (prof) {
-            OC_CUDA(cudaEventRecord(pr.b, s));
+            OC_CUDA(cudaEventRecordWithFlags(pr.b, s, persistent ? cudaEventRecordExternal : cudaEventRecordDefault));
             if (recs) recs->push_back(pr);
             else g->prof_pending.push_back(pr);
         }
     }
+    return OC_OK;
+}
+
+static int trace_event(cudaEvent_t& ev)
+{
+    if (g->tr_next < g->tr_pool.size()) { ev = g->tr_pool[g->tr_next++]; return OC_OK; }
+    OC_CUDA(cudaEventCreate(&ev));
+    g->tr_pool.push_back(ev);
+    g->tr_next = g->tr_pool.size();
+    return OC_OK;
+}
+
+// Open / close one traced span on stream s (no-ops without OC_FLAG_TRACE).
+static int trace_begin(int tile, int kind, cudaStream_t s)
+{
+    if (!(g->flags & OC_FLAG_TRACE)) return OC_OK;
+    Ctx::TraceRec r{tile, kind, nullptr, nullptr, 0.0};
+    int rc = trace_event(r.a);
+    if (!rc) rc = trace_event(r.b);
+    if (rc) return rc;
+    OC_CUDA(cudaEventRecord(r.a, s));
+    g->tr.push_back(r);
+    return OC_OK;
+}
+
+static int trace_end(cudaStream_t s, double bytes)
+{
+    if (!(g->flags & OC_FLAG_TRACE)) return OC_OK;
+    g->tr.back().bytes = bytes;
+    OC_CUDA(cudaEventRecord(g->tr.back().b, s));
+    return OC_OK;
+}
+
+static int collect_trace()
+{
+    g->tr_out.clear();
+    for (const auto& r : g->tr) {
+        float a = 0, b = 0;
+        OC_CUDA(cudaEventElapsedTime(&a, g->tr_t0, r.a));
+        OC_CUDA(cudaEventElapsedTime(&b, g->tr_t0, r.b));
+        g->tr_out.push_back({r.tile, r.kind, (double)a, (double)b, r.bytes});
+    }
+    g->tr.clear();
+    g->tr_next = 0;
     return OC_OK;
 }
 
@@ -602,9 +655,10 @@ static int execute()
     if ((size_t)P.nparams > g->h_params_cap) {
         host_free(g->h_params, true);
         g->h_params_cap = std::max<size_t>(P.nparams, 1024);
-        g->h_params = (double*)host_alloc(g->h_params_cap * 8, true);
+        g->h_params = (double*)host_alloc(g->h_params_cap * 12, true);
         if (!g->h_params) return fail(OC_ERR_NOMEM, "pinned parameter block");
     }
+    float* h_paramsf = (float*)(g->h_params + g->h_params_cap);
     if (g->h_results_cap < P.rp.size() || !g->h_results) {
         host_free(g->h_results, true);
         g->h_results_cap = std::max<size_t>(P.rp.size(), 64);
@@ -612,7 +666,10 @@ static int execute()
         if (!g->h_results) return fail(OC_ERR_NOMEM, "pinned result block");
     }
     for (int i = 0; i < P.L; ++i)
-        for (size_t j = 0; j < loops[i].params.size(); ++j) g->h_params[P.loop_param[i] + j] = loops[i].params[j];
+        for (size_t j = 0; j < loops[i].params.size(); ++j) {
+            g->h_params[P.loop_param[i] + j] = loops[i].params[j];
+            h_paramsf[P.loop_param[i] + j] = (float)loops[i].params[j];
+        }
     const long long sb = scratch_base(P);
 
     // a prefetch made for another plan must land before anything else touches slots
@@ -622,9 +679,20 @@ static int execute()
         if (!pf_match) g->pf.active = false;
     }
 
-    if (P.nparams > 0)
+    if (g->flags & OC_FLAG_TRACE) {
+        if (!g->tr_t0) OC_CUDA(cudaEventCreate(&g->tr_t0));
+        OC_CUDA(cudaEventRecord(g->tr_t0, s0));
+        OC_CUDA(cudaStreamWaitEvent(s1, g->tr_t0, 0));
+        OC_CUDA(cudaStreamWaitEvent(s2, g->tr_t0, 0));
+        g->tr.clear();
+        g->tr_next = 0;
+    }
+    if (P.nparams > 0) {
         OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.params_off, g->h_params, (size_t)P.nparams * 8,
                                 cudaMemcpyHostToDevice, s0));
+        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.paramsf_off, h_paramsf, (size_t)P.nparams * 4,
+                                cudaMemcpyHostToDevice, s0));
+    }
 
     const bool use_graphs = (g->flags & OC_FLAG_GRAPHS) != 0;
     GraphSet* gs = nullptr;
@@ -679,7 +747,12 @@ static int execute()
                 if (rc) return rc;
             }
         }
-        if (P.T > 0) { rc = run_compute(0); if (rc) return rc; }
+        if (P.T > 0) {
+            rc = trace_begin(0, 1, s0);
+            if (!rc) rc = run_compute(0);
+            if (!rc) rc = trace_end(s0, 0.0);
+            if (rc) return rc;
+        }
         for (const Loop& lp : loops)
             for (const Arg& ar : lp.args)
                 if (ar.access == OC_WRITE || ar.access == OC_RW) g->dats[ar.dat].host_valid = false;
@@ -694,6 +767,9 @@ static int execute()
             if (u >= 0 && u < T) {
                 if (p - 1 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_comp[p - 1], 0));
                 if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_down[p - 2], 0));
+                const double up0 = S.h2d_bytes;
+                rc = trace_begin(u, 0, s1);
+                if (rc) return rc;
                 for (size_t di = 0; di < P.dp.size(); ++di) {
                     const DatPlan& dp = P.dp[di];
                     const Dat& d = g->dats[dp.dat];
@@ -707,18 +783,25 @@ static int execute()
                         if (rc) return rc;
                     }
                 }
+                rc = trace_end(s1, S.h2d_bytes - up0);
+                if (rc) return rc;
                 OC_CUDA(cudaEventRecord(g->ev_up[u], s1));
             }
             if (p >= 0 && p < T) {
                 OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
                 if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
-                rc = run_compute(p);
+                rc = trace_begin(p, 1, s0);
+                if (!rc) rc = run_compute(p);
+                if (!rc) rc = trace_end(s0, 0.0);
                 if (rc) return rc;
                 OC_CUDA(cudaEventRecord(g->ev_comp[p], s0));
             }
             const int q = p - 1;
             if (q >= 0 && q < T) {
                 OC_CUDA(cudaStreamWaitEvent(s2, g->ev_comp[q], 0));
+                const double dn0 = S.d2h_bytes;
+                rc = trace_begin(q, 2, s2);
+                if (rc) return rc;
                 for (size_t di = 0; di < P.dp.size(); ++di) {
                     const DatPlan& dp = P.dp[di];
                     const Dat& d = g->dats[dp.dat];
@@ -728,6 +811,8 @@ static int execute()
                             if (rc) return rc;
                         }
                 }
+                rc = trace_end(s2, S.d2h_bytes - dn0);
+                if (rc) return rc;
                 OC_CUDA(cudaEventRecord(g->ev_down[q], s2));
             }
         }
@@ -762,6 +847,10 @@ static int execute()
     }
     if (!g->prof_pending.empty()) {
         rc = collect_profile();
+        if (rc) return rc;
+    }
+    if (!g->tr.empty()) {
+        rc = collect_trace();
         if (rc) return rc;
     }
     double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -940,6 +1029,8 @@ int oc_finalize(void)
             for (auto& v : kv.second.prof) for (auto& pr : v) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
         }
         for (auto e : g->ev_pool) cudaEventDestroy(e);
+        for (auto e : g->tr_pool) cudaEventDestroy(e);
+        if (g->tr_t0) cudaEventDestroy(g->tr_t0);
         for (auto e : g->ev_up) cudaEventDestroy(e);
         for (auto e : g->ev_comp) cudaEventDestroy(e);
         for (auto e : g->ev_down) cudaEventDestroy(e);
@@ -1097,7 +1188,7 @@ int oc_fetch_dat(int dat, void* host_out)
 int oc_set_flag(uint32_t flag, int on)
 {
     if (!g) return fail(OC_ERR_STATE, "oc_set_flag: no context");
-    if (flag & ~(OC_FLAG_CYCLIC | OC_FLAG_PREFETCH | OC_FLAG_GRAPHS | OC_FLAG_PROFILE))
+    if (flag & ~(OC_FLAG_CYCLIC | OC_FLAG_PREFETCH | OC_FLAG_GRAPHS | OC_FLAG_PROFILE | OC_FLAG_TRACE))
         return fail(OC_ERR_ARG, "oc_set_flag: flag");
     if (on) g->flags |= flag;
     else g->flags &= ~flag;
@@ -1131,6 +1222,15 @@ int oc_kernel_stats(int kernel_id, oc_kernel_stats_t* out)
     out->ms = k.ms;
     out->bytes = k.bytes;
     out->points = k.points;
+    return OC_OK;
+}
+
+int oc_trace(oc_trace_rec* out, int cap, int* n)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_trace: no context");
+    if (!n || (cap > 0 && !out)) return fail(OC_ERR_ARG, "oc_trace: null");
+    *n = (int)g->tr_out.size();
+    for (int i = 0; i < cap && i < *n; ++i) out[i] = g->tr_out[i];
     return OC_OK;
 }
 

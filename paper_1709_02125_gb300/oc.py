@@ -20,7 +20,8 @@ OC_OK, OC_ERR_ARG, OC_ERR_BUDGET, OC_ERR_CUDA, OC_ERR_TIMEOUT, OC_ERR_STATE, OC_
 OC_F64, OC_F32 = 0, 1
 OC_READ, OC_WRITE, OC_RW, OC_REDUCE = 1, 2, 3, 4
 OC_SUM, OC_MAX, OC_MIN = 0, 1, 2
-OC_FLAG_CYCLIC, OC_FLAG_PREFETCH, OC_FLAG_GRAPHS, OC_FLAG_DRYRUN, OC_FLAG_PROFILE = 0x1, 0x2, 0x4, 0x8, 0x10
+OC_FLAG_CYCLIC, OC_FLAG_PREFETCH, OC_FLAG_GRAPHS, OC_FLAG_DRYRUN, OC_FLAG_PROFILE, OC_FLAG_TRACE = \
+    0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 OC_PLAN_FIXED, OC_PLAN_AUTOTUNE, OC_PLAN_LEARNED = 0, 1, 2
 OC_K_COPY, OC_K_LINCOMB, OC_K_REDUCE, OC_K_HILO_ADD = 1, 2, 3, 4
 
@@ -32,7 +33,8 @@ DTYPES = {"f64": (OC_F64, np.float64), "f32": (OC_F32, np.float32)}
 
 EXPORTS = ["oc_init", "oc_finalize", "oc_decl_dat", "oc_decl_reduction", "oc_enqueue_loop", "oc_flush",
            "oc_reduce", "oc_fetch_dat", "oc_set_flag", "oc_set_tiling", "oc_stats", "oc_last_error",
-           "oc_plan_shape", "oc_plan_ranges", "oc_plan_dat", "oc_kernel_stats", "oc_kernel_stats_reset"]
+           "oc_plan_shape", "oc_plan_ranges", "oc_plan_dat", "oc_kernel_stats", "oc_kernel_stats_reset",
+           "oc_trace"]
 
 
 class OcArg(ctypes.Structure):
@@ -54,6 +56,11 @@ class OcStats(ctypes.Structure):
 class OcKernelStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
                 ("points", ctypes.c_double)]
+
+
+class OcTraceRec(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("kind", ctypes.c_int), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class OcError(RuntimeError):
@@ -90,6 +97,7 @@ def load():
     L.oc_plan_dat.argtypes = [I, IP, IP, IP, I, IP, IP, I, IP]
     L.oc_kernel_stats.argtypes = [I, ctypes.POINTER(OcKernelStats)]
     L.oc_kernel_stats_reset.argtypes = []
+    L.oc_trace.argtypes = [ctypes.POINTER(OcTraceRec), I, IP]
     for name in EXPORTS:
         if name != "oc_last_error":
             getattr(L, name).restype = I
@@ -224,6 +232,15 @@ class Executor:
             kid = physics.KERNELS[kernel]
         _check(self.L.oc_kernel_stats(kid, ctypes.byref(k)))
         return {f: getattr(k, f) for f, _ in OcKernelStats._fields_}
+
+    def trace(self) -> list:
+        """Time line of the last flush (needs OC_FLAG_TRACE): (tile, kind, start, end, bytes)."""
+        n = ctypes.c_int()
+        _check(self.L.oc_trace(None, 0, ctypes.byref(n)))
+        arr = (OcTraceRec * max(1, n.value))()
+        _check(self.L.oc_trace(arr, n.value, ctypes.byref(n)))
+        kinds = ("upload", "compute", "download")
+        return [(r.tile, kinds[r.kind], r.start_ms, r.end_ms, r.bytes) for r in arr[:n.value]]
 
     def kernel_stats_reset(self):
         _check(self.L.oc_kernel_stats_reset())

@@ -1,0 +1,138 @@
+"""2-D compressible Euler workload (stand-in for CloverLeaf 2-D, arXiv 1709.02125 Sec. 5.1).
+
+Ideal gas, gamma = 1.4, periodic unit square, n x n cells (dx = dy = 1/n). Background
+rho = 0.2, specific internal energy e = 1.0, at rest; a centred square of side n/4
+with rho = 1.0, e = 2.5. The square's edges are smoothed over `edge` cells with a tanh
+profile so that the non-TVD MacCormack scheme stays positive. CFL 0.5, fourth-order
+dissipation eps4 = 1/64.
+
+`chain_loops` is the user code of one time step as a loop chain for the executor:
+34 datasets -- two sets of conserved variables (ping-pong), primitives, fluxes,
+predicted state, its primitives and fluxes -- and 7 loops per step, the last being the
+CFL min-reduction that ends the chain. x is periodic inside each row (kernels wrap);
+y, the tiled axis, is periodic through halo rows refreshed at the start of every
+chain (deep ghosts), into which the loops extend their ranges.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Tuple
+
+import numpy as np
+
+from .spec import READ, REDUCE, RW, WRITE, Arg, DatSpec, Loop, RedSpec
+
+GAMMA = 1.4
+CFL = 0.5
+EPS4 = 1.0 / 64.0
+SEED = 1709 + 3
+
+
+def initial(n: int, edge: float = 1.5) -> np.ndarray:
+    """Conserved state (4, n, n): rho, mx, my, E."""
+    x = (np.arange(n) + 0.5) / n
+    half = 0.125
+    w = edge / n
+
+    def prof(c):
+        return 0.5 * (np.tanh((c - (0.5 - half)) / w) - np.tanh((c - (0.5 + half)) / w))
+
+    s = np.outer(prof(x), prof(x))          # 1 inside the square, 0 outside
+    rho = 0.2 + 0.8 * s
+    e = 1.0 + 1.5 * s
+    U = np.zeros((4, n, n))
+    U[0] = rho
+    U[3] = rho * e
+    return U
+
+
+def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = False) -> List[DatSpec]:
+    """Datasets of the chain. Conserved sets A and B have halo 2 in y; the rest 1."""
+    per = (0, 1)
+    ds = []
+    names_c = ["r", "mx", "my", "E"]
+
+    def dat(name, hlo, hhi, init=None):
+        ds.append(DatSpec(name, (n, n), (0, hlo), (0, hhi), dtype, per, init))
+
+    def pad(a):
+        out = np.zeros((n + 4, n))
+        out[2:n + 2] = a
+        return out
+
+    for k, c in enumerate(names_c):
+        init = pad(U0[k]) if U0 is not None else None
+        if mixed:
+            hi = init.astype(np.float32) if init is not None else None
+            lo = (init - hi.astype(np.float64)).astype(np.float32) if init is not None else None
+            dat(f"A_{c}", 2, 2, hi)
+            dat(f"L_{c}", 2, 2, lo)
+            dat(f"D_{c}", 0, 0)
+        else:
+            dat(f"A_{c}", 2, 2, init)
+            dat(f"B_{c}", 2, 2)
+    for c in ("u", "v", "p"):
+        dat(c, 1, 1)
+    for k in range(4):
+        dat(f"F{k}", 1, 1)
+        dat(f"G{k}", 1, 1)
+        dat(f"S{k}", 1, 0)
+        dat(f"H{k}", 1, 0)
+        dat(f"K{k}", 1, 0)
+    for c in ("us", "vs", "ps"):
+        dat(c, 1, 0)
+    return ds
+
+
+def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool = False,
+                red: str = "dtmin") -> List[Loop]:
+    """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L)."""
+    lx = ly = dt * n
+    c = ["r", "mx", "my", "E"]
+    U = [f"{src}_{k}" for k in c]
+    S = [f"S{k}" for k in range(4)]
+    o = [(0, 0)]
+    loops = [
+        Loop("euler_prim", (0, -1), (n, n + 1), [Arg(u, READ) for u in U] +
+             [Arg("u", WRITE), Arg("v", WRITE), Arg("p", WRITE)], [GAMMA]),
+        Loop("euler_flux", (0, -1), (n, n + 1), [Arg(u, READ) for u in U] +
+             [Arg("u", READ), Arg("v", READ), Arg("p", READ)] +
+             [Arg(f"F{k}", WRITE) for k in range(4)] + [Arg(f"G{k}", WRITE) for k in range(4)], []),
+        Loop("euler_pred", (0, -1), (n, n), [Arg(u, READ) for u in U] +
+             [Arg(f"F{k}", READ, [(0, 0), (1, 0)]) for k in range(4)] +
+             [Arg(f"G{k}", READ, [(0, 0), (0, 1)]) for k in range(4)] +
+             [Arg(s, WRITE) for s in S], [lx, ly]),
+        Loop("euler_prim", (0, -1), (n, n), [Arg(s, READ) for s in S] +
+             [Arg("us", WRITE), Arg("vs", WRITE), Arg("ps", WRITE)], [GAMMA]),
+        Loop("euler_flux", (0, -1), (n, n), [Arg(s, READ) for s in S] +
+             [Arg("us", READ), Arg("vs", READ), Arg("ps", READ)] +
+             [Arg(f"H{k}", WRITE) for k in range(4)] + [Arg(f"K{k}", WRITE) for k in range(4)], []),
+    ]
+    cross = [(0, 0), (1, 0), (-1, 0), (2, 0), (-2, 0), (0, 1), (0, -1), (0, 2), (0, -2)]
+    corr_in = ([Arg(u, READ, cross) for u in U] + [Arg(s, READ) for s in S] +
+               [Arg(f"H{k}", READ, [(0, 0), (-1, 0)]) for k in range(4)] +
+               [Arg(f"K{k}", READ, [(0, 0), (0, -1)]) for k in range(4)])
+    if not mixed:
+        loops.append(Loop("euler_corr", (0, 0), (n, n), corr_in + [Arg(f"{dst}_{k}", WRITE) for k in c],
+                          [lx, ly, EPS4, 0.0]))
+        loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"{dst}_{k}", READ) for k in c] + [Arg(red, REDUCE)],
+                          [GAMMA, 1.0 / n, 1.0 / n]))
+    else:
+        loops.append(Loop("euler_corr", (0, 0), (n, n), corr_in + [Arg(f"D_{k}", WRITE) for k in c],
+                          [lx, ly, EPS4, 1.0]))
+        for k in c:
+            loops.append(Loop("hilo_add", (0, 0), (n, n), [Arg(f"A_{k}", RW), Arg(f"L_{k}", RW),
+                                                           Arg(f"D_{k}", READ)], [1.0]))
+        loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"A_{k}", READ) for k in c] +
+                          [Arg(f"L_{k}", READ) for k in c] + [Arg(red, REDUCE)], [GAMMA, 1.0 / n, 1.0 / n]))
+    return loops
+
+
+def totals_loops(n: int, names: List[str], reds: List[str], lo_names: List[str] = None) -> List[Loop]:
+    """FP64 totals (sum over the interior) of the conserved variables (hi + lo if mixed)."""
+    out = []
+    for k, (nm, r) in enumerate(zip(names, reds)):
+        args = [Arg(nm, READ)]
+        if lo_names:
+            args.append(Arg(lo_names[k], READ))
+        out.append(Loop("reduce", (0, 0), (n, n), args + [Arg(r, REDUCE)], [0.0]))
+    return out
