@@ -265,9 +265,12 @@ const char* oc_last_error(void);
  *   of loop i in tile t (s == e: loop i does nothing in tile t).
  * oc_plan_dat: k-th dataset of the chain (0 <= k < ndats): its handle, slab rows S
  *   (rows are stored at slot (y - y_first) mod S; S = all rows when in-core), and
- *   the row intervals copied per tile: up[3*j] = tile, up[3*j+1..2] = [a, b) for
- *   j < *nup (likewise down). Capacities in cap_up / cap_down triples; if too small
- *   OC_ERR_ARG is returned and *nup / *ndown hold the required counts. */
+ *   the row intervals copied per tile, five ints each: up[5*j] = tile,
+ *   up[5*j+1..2] = slow rows [a, b), up[5*j+3..4] = [x0, x1): x0 == x1 means whole
+ *   rows; x0 < x1 means the rows are first written over x in [x0, x1) (Sec. 4.1
+ *   "write-first") and only the columns outside it are uploaded; j < *nup (likewise
+ *   down, always whole rows). Capacities cap_up / cap_down count intervals; if too
+ *   small OC_ERR_ARG is returned and *nup / *ndown hold the required counts. */
 int oc_plan_shape(int* ntiles, int* nloops, int* ndats, int* tile_height, int* depth,
                   int* slow_rows);
 int oc_plan_ranges(int* se);

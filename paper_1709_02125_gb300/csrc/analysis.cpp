@@ -177,9 +177,16 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
             }
         }
     // program-order state per row: 0 untouched, 1 first access a full-row write,
-    // 2 first access anything else (a read or a partial write)
+    // 2 first access anything else (a read, or a write that leaves part of the row
+    // other than x columns), 3 first access a write over x in [wx0, wx1) and the full
+    // extent of the other non-slow axes (only the x columns outside it are uploaded)
     std::vector<std::vector<uint8_t>> state(ND), written(ND);
-    for (int d = 0; d < ND; ++d) { state[d].assign(P.dp[d].nrows, 0); written[d].assign(P.dp[d].nrows, 0); }
+    for (int d = 0; d < ND; ++d) {
+        state[d].assign(P.dp[d].nrows, 0);
+        written[d].assign(P.dp[d].nrows, 0);
+        P.dp[d].wx0.assign(P.dp[d].nrows, 0);
+        P.dp[d].wx1.assign(P.dp[d].nrows, 0);
+    }
     for (const Loop& lp : loops) {
         int lo = lp.lo[sa], hi = lp.hi[sa];
         if (lo >= hi) continue;
@@ -194,11 +201,22 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
         for (const Arg& ar : lp.args)
             if (ar.access != OC_REDUCE && is_write(ar.access)) {
                 int d = P.dat_index[ar.dat];
-                const DatPlan& dp = P.dp[d];
-                uint8_t st = full_row_write(lp, dats[ar.dat]) ? 1 : 2;
+                DatPlan& dp = P.dp[d];
+                const Dat& dd = dats[ar.dat];
+                uint8_t st = full_row_write(lp, dd) ? 1 : 2;
+                if (st == 2 && ar.access == OC_WRITE) {
+                    bool others_full = true;
+                    for (int a = 1; a < dd.ndim - 1; ++a)
+                        others_full = others_full && lp.lo[a] <= -dd.hlo[a] && lp.hi[a] >= dd.size[a] + dd.hhi[a];
+                    if (others_full) st = 3;
+                }
                 for (long long y = std::max(lo, dp.y0); y < std::min(hi, dp.y0 + dp.nrows); ++y) {
-                    if (!state[d][y - dp.y0]) state[d][y - dp.y0] = st;
-                    written[d][y - dp.y0] = 1;
+                    const long long r = y - dp.y0;
+                    if (!state[d][r]) {
+                        state[d][r] = st;
+                        if (st == 3) { dp.wx0[r] = std::max(lp.lo[0], -dd.hlo[0]); dp.wx1[r] = std::min(lp.hi[0], dd.size[0] + dd.hhi[0]); }
+                    }
+                    written[d][r] = 1;
                 }
             }
     }
@@ -207,24 +225,29 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
         DatPlan& dp = P.dp[d];
         for (int r = 0; r < dp.nrows; ++r) {
             if (dp.first[r] < 0) continue;
-            dp.need_up[r] = state[d][r] == 2;
-            dp.dl[r] = written[d][r] && !(cyclic && state[d][r] == 1);
+            const uint8_t st = state[d][r];
+            dp.need_up[r] = st == 2 ? 1 : (st == 3 ? 2 : 0);
+            dp.dl[r] = written[d][r] && !(cyclic && (st == 1 || st == 3));
         }
-        // group rows into per-tile intervals
-        auto group = [&](const std::vector<uint8_t>& need, const std::vector<int>& tile,
+        // group rows into per-tile intervals (same tile, same copy kind and columns)
+        auto group = [&](const std::vector<uint8_t>& need, const std::vector<int>& tile, bool cols,
                          std::vector<Interval>& out) {
             out.clear();
             int r = 0;
+            auto key = [&](int q) { return cols && need[q] == 2 ? std::make_pair(dp.wx0[q], dp.wx1[q]) : std::make_pair(0, 0); };
             while (r < dp.nrows) {
                 if (!need[r]) { ++r; continue; }
                 int t = tile[r], a = r;
-                while (r < dp.nrows && need[r] && tile[r] == t) ++r;
-                out.push_back({t, a + dp.y0, r + dp.y0});
+                const uint8_t kind = need[r];
+                const auto kx = key(r);
+                while (r < dp.nrows && need[r] == kind && tile[r] == t && key(r) == kx) ++r;
+                Interval iv{t, a + dp.y0, r + dp.y0, kx.first, kx.second};
+                out.push_back(iv);
             }
             std::stable_sort(out.begin(), out.end(), [](const Interval& x, const Interval& y) { return x.t < y.t; });
         };
-        group(dp.need_up, dp.first, dp.up);
-        group(dp.dl, dp.last, dp.down);
+        group(dp.need_up, dp.first, true, dp.up);
+        group(dp.dl, dp.last, false, dp.down);
 
         // slab rows: largest span of rows live in one phase. Phase p computes tile p,
         // uploads tile p + k, downloads tile p - 1. A row is live from the phase of its

@@ -15,38 +15,15 @@
 #include <cuda_runtime.h>
 
 #include "../../include/oc.h"
+#include "kcommon.cuh"
 #include "launch.h"
 
 namespace oc {
 
 namespace {
 
-constexpr int kThreadsX = 128;
+using namespace dev;
 constexpr int kRows = 4;
-
-__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// Pointer to element (x + dx, yl + dy) of the x-line of slot `slot`.
-template <typename T>
-__device__ __forceinline__ const T* col_ptr(const DView& v, int x, int yl)
-{
-    if (v.periodic & 1) x = wrap1(x, v.nx);
-    if (v.periodic & 2) yl = wrap1(yl, v.ny);
-    return reinterpret_cast<const T*>(v.base) + (long long)(yl + v.oy) * v.pitch + v.ox + x;
-}
-
-__device__ __forceinline__ int first_slot(const DView& v, int s)
-{
-    int slot = v.slot0 + (s - v.W0);
-    return slot >= v.S ? slot - v.S : slot;
-}
-
-template <typename T>
-__device__ __forceinline__ const T* params_of(const LaunchDesc& d);
-template <>
-__device__ __forceinline__ const float* params_of<float>(const LaunchDesc& d) { return d.paramsf; }
-template <>
-__device__ __forceinline__ const double* params_of<double>(const LaunchDesc& d) { return d.params; }
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -188,39 +165,6 @@ __global__ void __launch_bounds__(kThreadsX) k_hilo_add(const __grid_constant__ 
         if (++sl == d.v[1].S) sl = 0;
         if (++su == d.v[2].S) su = 0;
     }
-}
-
-__device__ __forceinline__ double red_identity(int op)
-{
-    return op == OC_SUM ? 0.0 : (op == OC_MAX ? -__longlong_as_double(0x7ff0000000000000LL)
-                                              : __longlong_as_double(0x7ff0000000000000LL));
-}
-
-__device__ __forceinline__ double red_apply(int op, double a, double b)
-{
-    if (op == OC_SUM) return a + b;
-    if (op == OC_MAX) return b > a ? b : a;
-    return b < a ? b : a;
-}
-
-constexpr int kRedThreads = 256;
-
-// Fixed-shape block fold: each thread folds its strided elements in order, then a
-// fixed shuffle tree per warp and a fixed tree over the warps.
-__device__ __forceinline__ double block_fold(double acc, int op)
-{
-    __shared__ double sm[kRedThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sm[w] = acc;
-    __syncthreads();
-    if (w == 0) {
-        acc = l < kRedThreads / 32 ? sm[l] : red_identity(op);
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
-    }
-    return acc;
 }
 
 // One block per (chunk of kRedChunk points of a slow row, slow row). The partial of

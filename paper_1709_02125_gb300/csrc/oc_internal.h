@@ -66,7 +66,10 @@ struct Loop {
     }
 };
 
-struct Interval { int t, a, b; };  // tile t moves slow rows [a, b)
+// Tile t moves slow rows [a, b). x0 == x1: whole rows. x0 < x1: the rows were first
+// written over x in [x0, x1) (all other non-slow axes complete), so only the columns
+// outside [x0, x1) -- the halo the writer leaves alone -- are copied.
+struct Interval { int t, a, b, x0 = 0, x1 = 0; };
 
 struct DatPlan {
     int dat = -1;
@@ -75,7 +78,8 @@ struct DatPlan {
     long long off = 0;         // arena byte offset of the slab
     std::vector<Interval> up, down;
     std::vector<int> first, last;      // per row: first / last tile touching it, -1 if none
-    std::vector<uint8_t> need_up, dl;  // per row: uploaded / downloaded by this chain
+    std::vector<uint8_t> need_up, dl;  // per row: uploaded (1 whole, 2 columns) / downloaded
+    std::vector<int> wx0, wx1;         // per row with need_up == 2: x range of its first writer
 };
 
 struct RedPlan {

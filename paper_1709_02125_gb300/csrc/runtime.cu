@@ -97,7 +97,7 @@ struct Ctx {
     std::vector<char> red_has;
     std::vector<Loop> queue;
     std::unordered_map<uint64_t, Plan> plans;       // by plan signature
-    std::unordered_map<uint64_t, std::pair<int, int>> choice;  // chain signature -> (h, depth)
+    std::unordered_map<uint64_t, Plan*> chosen;      // chain shape + settings -> plan
     std::unordered_map<uint64_t, std::vector<std::vector<LaunchDesc>>> descs;  // plan sig -> tiles
     std::unordered_map<uint64_t, GraphSet> graphs;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
@@ -184,18 +184,38 @@ static void host_free(void* p, bool pinned)
 // ---------------------------------------------------------------------------------
 // Copies between the pinned store and a slab. Rows [a, b) of dataset d go to slots
 // (y - y0) mod S of the slab at `slab`; a range crossing the slab end is split.
+// With x0 < x1 (uploads of rows first written over x in [x0, x1)) only the x columns
+// outside [x0, x1) are copied: two strided copies over every x-line of the rows.
 static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cudaStream_t s,
-                     double& bytes)
+                     double& bytes, int x0 = 0, int x1 = 0)
 {
     const long long rb = d.row_bytes();
+    const size_t lp = (size_t)d.pitch * d.esz;
     while (a < b) {
         int slot = (int)(((long long)(a - d.y0)) % S);
         int n = std::min(b - a, S - slot);
         char* dev = slab + (long long)slot * rb;
         char* host = (char*)d.host + (long long)(a - d.y0) * rb;
-        if (up) OC_CUDA(cudaMemcpyAsync(dev, host, (size_t)n * rb, cudaMemcpyHostToDevice, s));
-        else OC_CUDA(cudaMemcpyAsync(host, dev, (size_t)n * rb, cudaMemcpyDeviceToHost, s));
-        bytes += (double)n * rb;
+        if (x0 < x1) {
+            const cudaMemcpyKind kind = up ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+            const size_t lines = (size_t)n * d.ylines;
+            const long long c0 = d.ox - d.hlo[0];                       // first column (x = -hlo)
+            const long long cl = (long long)x0 + d.hlo[0];              // left strip width
+            const long long cr = (long long)d.size[0] + d.hhi[0] - x1;  // right strip width
+            const long long c1 = d.ox + x1;
+            char* dsts[2] = {up ? dev + c0 * d.esz : host + c0 * d.esz, up ? dev + c1 * d.esz : host + c1 * d.esz};
+            const char* srcs[2] = {up ? host + c0 * d.esz : dev + c0 * d.esz, up ? host + c1 * d.esz : dev + c1 * d.esz};
+            const long long w[2] = {cl, cr};
+            for (int k = 0; k < 2; ++k)
+                if (w[k] > 0) {
+                    OC_CUDA(cudaMemcpy2DAsync(dsts[k], lp, srcs[k], lp, (size_t)w[k] * d.esz, lines, kind, s));
+                    bytes += (double)w[k] * d.esz * lines;
+                }
+        } else {
+            if (up) OC_CUDA(cudaMemcpyAsync(dev, host, (size_t)n * rb, cudaMemcpyHostToDevice, s));
+            else OC_CUDA(cudaMemcpyAsync(host, dev, (size_t)n * rb, cudaMemcpyDeviceToHost, s));
+            bytes += (double)n * rb;
+        }
         a += n;
     }
     return OC_OK;
@@ -491,10 +511,9 @@ static bool reads_ghosts(const Plan& P, int di)
 }
 
 // ---------------------------------------------------------------------------------
-static int select_plan(const std::vector<Loop>& loops, Plan*& out)
+static int select_plan_uncached(const std::vector<Loop>& loops, uint64_t csig, Plan*& out)
 {
     std::string err;
-    const uint64_t csig = chain_signature(loops, g->dats, g->flags);
     // in-core (resident) mode when every declared dataset fits with the scratch
     Plan inc;
     build_plan(loops, g->dats, g->red_ops, 0, 3, g->flags, true, inc, err);
@@ -517,26 +536,16 @@ static int select_plan(const std::vector<Loop>& loops, Plan*& out)
     }
     if (g->resident_mode) { int r = leave_resident_mode(); if (r) return r; }
 
-    int h = 0, depth = 3;
-    auto ch = g->choice.find(csig);
-    if (g->force_h > 0 || g->force_depth > 0 || ch == g->choice.end()) {
-        depth = g->force_depth > 0 ? g->force_depth : 3;
-        if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED) {
-            int ph = 0, pd = 0;
-            if (planner_choose(loops, g->dats, g->red_ops, g->flags, g->budget, g->planner_mode, ph, pd)) {
-                h = ph; depth = pd;
-            }
+    int h = 0, depth = g->force_depth > 0 ? g->force_depth : 3;
+    if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED) {
+        int ph = 0, pd = 0;
+        if (planner_choose(loops, g->dats, g->red_ops, g->flags, g->budget, g->planner_mode, ph, pd)) {
+            h = ph;
+            depth = pd;
         }
-        if (h <= 0) {
-            if (g->force_h > 0) h = g->force_h;
-            else h = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
-        }
-        if (h <= 0) return fail(OC_ERR_BUDGET, "device budget of %lld bytes cannot hold one tile of height 1", g->budget);
-        if (g->force_h <= 0 && g->force_depth <= 0) g->choice[csig] = {h, depth};
-    } else {
-        h = ch->second.first;
-        depth = ch->second.second;
     }
+    if (h <= 0) h = g->force_h > 0 ? g->force_h : fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
+    if (h <= 0) return fail(OC_ERR_BUDGET, "device budget of %lld bytes cannot hold one tile of height 1", g->budget);
     Plan P;
     build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err);
     if (P.arena_bytes > g->budget)
@@ -545,6 +554,25 @@ static int select_plan(const std::vector<Loop>& loops, Plan*& out)
     auto it = g->plans.find(P.sig);
     if (it == g->plans.end()) it = g->plans.emplace(P.sig, std::move(P)).first;
     out = &it->second;
+    (void)csig;
+    return OC_OK;
+}
+
+// Plan of a chain: the choice (in-core or streamed, tile height, depth) is made once per
+// chain shape, tiling override, planner mode and number of declared datasets.
+static int select_plan(const std::vector<Loop>& loops, Plan*& out)
+{
+    uint64_t key = chain_signature(loops, g->dats, g->flags);
+    key ^= ((uint64_t)(uint32_t)g->force_h << 20) ^ ((uint64_t)g->force_depth << 52) ^
+           ((uint64_t)g->planner_mode << 60) ^ ((uint64_t)g->dats.size() * 0xC2B2AE3D27D4EB4Full);
+    auto it = g->chosen.find(key);
+    if (it != g->chosen.end() && (!it->second->incore || g->resident_mode)) {
+        out = it->second;
+        return OC_OK;
+    }
+    int rc = select_plan_uncached(loops, key, out);
+    if (rc) return rc;
+    g->chosen[key] = out;
     return OC_OK;
 }
 
@@ -582,15 +610,16 @@ static int issue_prefetch(const Plan& P)
                 bool ghost = (d.periodic & (1 << sa)) && (y < 0 || y >= d.size[sa]);
                 if (ghost) continue;
                 if (busy[r % dp.S] || (dp.dl[r] && dp.last[r] >= T - 1)) { ok = false; break; }
-                if (!rows.empty() && rows.back().b == y) rows.back().b = y + 1;
-                else rows.push_back({0, y, y + 1});
+                if (!rows.empty() && rows.back().b == y && rows.back().x0 == iv.x0 && rows.back().x1 == iv.x1)
+                    rows.back().b = y + 1;
+                else rows.push_back({0, y, y + 1, iv.x0, iv.x1});
             }
             if (!ok) break;
         }
         if (!ok) continue;
         for (const Interval& iv : rows) {
             double b = 0;
-            int r = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, true, g->st[1], b);
+            int r = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, true, g->st[1], b, iv.x0, iv.x1);
             if (r) return r;
             g->pf.bytes += b;
         }
@@ -764,6 +793,19 @@ static int execute()
         const int T = P.T, k = P.depth - 2;
         for (int p = -k; p <= T; ++p) {
             const int u = p + k;
+            // Issue order inside a phase: with lookahead (k >= 1) compute and download
+            // go first so the compute stream is fed before the host spends time on the
+            // upload calls; with k == 0 the upload of tile p must be issued before the
+            // compute that waits for it.
+            if (k >= 1 && p >= 0 && p < T) {
+                OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
+                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
+                rc = trace_begin(p, 1, s0);
+                if (!rc) rc = run_compute(p);
+                if (!rc) rc = trace_end(s0, 0.0);
+                if (rc) return rc;
+                OC_CUDA(cudaEventRecord(g->ev_comp[p], s0));
+            }
             if (u >= 0 && u < T) {
                 if (p - 1 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_comp[p - 1], 0));
                 if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_down[p - 2], 0));
@@ -778,7 +820,7 @@ static int execute()
                     for (const Interval& iv : dp.up) {
                         if (iv.t != u) continue;
                         rc = for_missing(iv, have, [&](int a, int b) {
-                            return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes);
+                            return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes, iv.x0, iv.x1);
                         });
                         if (rc) return rc;
                     }
@@ -787,7 +829,7 @@ static int execute()
                 if (rc) return rc;
                 OC_CUDA(cudaEventRecord(g->ev_up[u], s1));
             }
-            if (p >= 0 && p < T) {
+            if (k == 0 && p >= 0 && p < T) {
                 OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
                 if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
                 rc = trace_begin(p, 1, s0);
@@ -1277,8 +1319,9 @@ int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup, 
     if (ndown) *ndown = (int)dp.down.size();
     if ((int)dp.up.size() > cap_up || (int)dp.down.size() > cap_down)
         return fail(OC_ERR_ARG, "oc_plan_dat: capacity too small");
-    for (size_t j = 0; j < dp.up.size(); ++j) { up[3 * j] = dp.up[j].t; up[3 * j + 1] = dp.up[j].a; up[3 * j + 2] = dp.up[j].b; }
-    for (size_t j = 0; j < dp.down.size(); ++j) { down[3 * j] = dp.down[j].t; down[3 * j + 1] = dp.down[j].a; down[3 * j + 2] = dp.down[j].b; }
+    auto put = [](int* o, const Interval& iv) { o[0] = iv.t; o[1] = iv.a; o[2] = iv.b; o[3] = iv.x0; o[4] = iv.x1; };
+    for (size_t j = 0; j < dp.up.size(); ++j) put(up + 5 * j, dp.up[j]);
+    for (size_t j = 0; j < dp.down.size(); ++j) put(down + 5 * j, dp.down[j]);
     return OC_OK;
 }
 

@@ -257,14 +257,14 @@ class Executor:
         for k in range(ND):
             dat, S, nup, ndn = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
             cap = 1 << 16
-            up = np.zeros(3 * cap, dtype=np.int32)
-            dn = np.zeros(3 * cap, dtype=np.int32)
+            up = np.zeros(5 * cap, dtype=np.int32)
+            dn = np.zeros(5 * cap, dtype=np.int32)
             IP = ctypes.POINTER(ctypes.c_int)
             _check(self.L.oc_plan_dat(k, ctypes.byref(dat), ctypes.byref(S), up.ctypes.data_as(IP), cap,
                                       ctypes.byref(nup), dn.ctypes.data_as(IP), cap, ctypes.byref(ndn)))
             dats.append({"dat": dat.value, "S": S.value,
-                         "up": up[:3 * nup.value].reshape(-1, 3).copy(),
-                         "down": dn[:3 * ndn.value].reshape(-1, 3).copy()})
+                         "up": up[:5 * nup.value].reshape(-1, 5).copy(),
+                         "down": dn[:5 * ndn.value].reshape(-1, 5).copy()})
         return {"tiles": T, "loops": L_, "tile_height": h, "depth": depth, "slow_rows": span,
                 "ranges": se[:T * L_ * 2].reshape(T, L_, 2).copy(), "dats": dats}
 

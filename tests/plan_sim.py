@@ -123,10 +123,10 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
         """rows touched in phase p per dataset: uploads of p+k, compute of p, downloads of p-1"""
         rows = {n: set() for n in slabs}
         for n, sl in slabs.items():
-            for t, a, b in sl["plan"]["up"]:
+            for t, a, b, _, _ in sl["plan"]["up"]:
                 if t == p + k:
                     rows[n].update(range(a, b))
-            for t, a, b in sl["plan"]["down"]:
+            for t, a, b, _, _ in sl["plan"]["down"]:
                 if t == p - 1:
                     rows[n].update(range(a, b))
         if 0 <= p < T:
@@ -151,10 +151,19 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
         u = p + k
         if 0 <= u < T:
             for n, sl in slabs.items():
-                for t, a, b in sl["plan"]["up"]:
+                for t, a, b, x0, x1 in sl["plan"]["up"]:
                     if t == u:
+                        hx = specs[n].halo_lo[0]
                         for y in range(a, b):
-                            sl["data"][slot(sl, y)] = host[n].a[y - sl["y0"]]
+                            row = host[n].a[y - sl["y0"]]
+                            if x0 < x1:
+                                # first written over [x0, x1): only the other columns
+                                # travel; the written part holds garbage until then
+                                new = np.full_like(row, np.nan)
+                                new[..., :x0 + hx] = row[..., :x0 + hx]
+                                new[..., x1 + hx:] = row[..., x1 + hx:]
+                                row = new
+                            sl["data"][slot(sl, y)] = row
                             sl["tag"][slot(sl, y)] = y
         if 0 <= p < T:
             for i, lp in enumerate(loops):
@@ -204,7 +213,7 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
         q = p - 1
         if 0 <= q < T:
             for n, sl in slabs.items():
-                for t, a, b in sl["plan"]["down"]:
+                for t, a, b, _, _ in sl["plan"]["down"]:
                     if t == q:
                         for y in range(a, b):
                             assert sl["tag"][slot(sl, y)] == y, f"download of {n} row {y}: slot holds another row"

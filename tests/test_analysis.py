@@ -81,6 +81,7 @@ def test_random_chain_plans_are_legal(lib, seed, h, depth):
 def test_random_chain_simulation_matches_oracle(lib, oracle_lib, seed, h, depth):
     dats, reds, loops = random_chain.build(n=24, nfields=8, nloops=16, seed=200 + seed)
     plan, _, names = dry(1 << 30, dats, reds, loops, h=h, depth=depth)
+    assert any(x0 < x1 for d in plan["dats"] for _, _, _, x0, x1 in d["up"])  # write-first columns occur
     plan_sim.check_legality(plan, loops)
     got, gred = plan_sim.simulate(plan, loops, dats, reds, oracle_lib, names)
     ref = oracle_lib.make_fields(dats)
@@ -140,10 +141,12 @@ def test_write_first_and_read_only_copies(lib):
         by = {d["dat"]: d for d in plan["dats"]}
         a, t, b = by[names["a"]], by[names["t"]], by[names["b"]]
         assert len(a["up"]) > 0 and len(a["down"]) == 0          # read-only: never downloaded
-        up_rows = {y for _, lo, hi in t["up"] for y in range(lo, hi)}
+        up_rows = {y for _, lo, hi, _, _ in t["up"] for y in range(lo, hi)}
         assert up_rows <= {-1, n}                                 # only halo rows it reads unwritten
         assert (len(t["down"]) > 0) == t_down
-        assert len(b["up"]) > 0                                   # partial-row write keeps the halo
+        # b is first written over its interior columns: only its halo columns travel
+        assert len(b["up"]) > 0 and all(x0 == 0 and x1 == n for _, _, _, x0, x1 in b["up"])
+        assert (len(b["down"]) > 0) == t_down
 
 
 @pytest.mark.parametrize("bad", ["write_offset", "extent", "self_read", "lincomb_params", "mixed_dtype"])

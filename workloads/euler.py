@@ -86,7 +86,7 @@ def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = Fa
 def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool = False,
                 red: str = "dtmin") -> List[Loop]:
     """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L)."""
-    lx = ly = dt * n
+    lx = ly = dt / (1.0 / n)
     c = ["r", "mx", "my", "E"]
     U = [f"{src}_{k}" for k in c]
     S = [f"S{k}" for k in range(4)]
@@ -136,3 +136,44 @@ def totals_loops(n: int, names: List[str], reds: List[str], lo_names: List[str] 
             args.append(Arg(lo_names[k], READ))
         out.append(Loop("reduce", (0, 0), (n, n), args + [Arg(r, REDUCE)], [0.0]))
     return out
+
+
+def dt_loop(n: int, mixed: bool = False, src: str = "A", red: str = "dtmin") -> Loop:
+    c = ["r", "mx", "my", "E"]
+    args = [Arg(f"{src}_{k}", READ) for k in c]
+    if mixed:
+        args += [Arg(f"L_{k}", READ) for k in c]
+    return Loop("euler_dt", (0, 0), (n, n), args + [Arg(red, REDUCE)], [GAMMA, 1.0 / n, 1.0 / n])
+
+
+def run(ex, n: int, steps: int, mixed: bool = False, U0: np.ndarray = None, totals: bool = False):
+    """Drive `steps` time steps on an executor `ex` (decl_dat / decl_reduction /
+    enqueue / reduce). Returns (time steps used, name prefix of the final state,
+    per-step conserved totals if requested)."""
+    U0 = initial(n) if U0 is None else U0
+    for d in datasets(n, "f32" if mixed else "f64", U0, mixed):
+        ex.decl_dat(d)
+    ex.decl_reduction("dtmin", "min")
+    tot_names = [f"tot_{k}" for k in ("r", "mx", "my", "E")]
+    for t in tot_names:
+        ex.decl_reduction(t, "sum")
+    ex.enqueue(dt_loop(n, mixed))
+    dtmin = ex.reduce("dtmin")
+    src, dst = "A", "B"
+    dts, tots = [], []
+    for _ in range(steps):
+        dt = CFL * dtmin
+        dts.append(dt)
+        for lp in chain_loops(n, dt, src, dst, mixed):
+            ex.enqueue(lp)
+        out = "A" if mixed else dst
+        if totals:
+            for lp in totals_loops(n, [f"{out}_{k}" for k in ("r", "mx", "my", "E")], tot_names,
+                                   [f"L_{k}" for k in ("r", "mx", "my", "E")] if mixed else None):
+                ex.enqueue(lp)
+        dtmin = ex.reduce("dtmin")
+        if totals:
+            tots.append([ex.reduce(t) for t in tot_names])
+        if not mixed:
+            src, dst = dst, src
+    return dts, ("A" if mixed else src), tots

@@ -123,3 +123,15 @@ def chain_loops(n: int, steps: int = 1, mixed: bool = False, re: float = RE) -> 
             loops.append(Loop("ns_update", lo, hi, [Arg(c, RW) for c in CONS] + [Arg("d" + c, READ) for c in CONS],
                               [RK_B[s]]))
     return loops
+
+
+def run(ex, n: int, chains: int, steps_per_chain: int = 1, mixed: bool = False, U0: np.ndarray = None):
+    """Drive `chains` chains of `steps_per_chain` RK3 steps on an executor `ex`."""
+    U0 = initial(n) if U0 is None else U0
+    for d in datasets(n, steps_per_chain, "f32" if mixed else "f64", U0, mixed):
+        ex.decl_dat(d)
+    loops = chain_loops(n, steps_per_chain, mixed)
+    for _ in range(chains):
+        for lp in loops:
+            ex.enqueue(lp)
+        ex.flush()
