@@ -277,6 +277,31 @@ int oc_plan_ranges(int* se);
 int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
                 int* down, int cap_down, int* ndown);
 
+/* ---- tile planner (spec addition (a); the paper sizes tiles by the fast-memory
+ * size only, Sec. 4) ----------------------------------------------------------------
+ * Features of a chain, 8 floats: log2(loops), datasets used, slow-axis stencil radius,
+ * bytes per cell, budget / footprint, dimensions, log2(footprint bytes), log2(slow rows).
+ * oc_planner_features: features of the most recently planned chain.
+ * oc_autotune_result: the table of the last autotuned chain (OC_PLAN_AUTOTUNE, or
+ *   OC_PLAN_LEARNED without a network), 5 doubles per candidate: tile height, depth,
+ *   device ms of the chain, grid index (height = round(hmax * {1, 3/4, 1/2, 3/8, 1/4,
+ *   3/16, 1/8, 1/16}[index])), hmax (largest fitting height at that depth). *n = rows.
+ * oc_planner_load: install the network used by OC_PLAN_LEARNED: oc_mlp_nparams() floats
+ *   and the features' standardisation (x - mean) / std. Outputs y0 = log2(h / hmax),
+ *   y1 = depth, snapped to the grid. Applies to chains planned afterwards.
+ * oc_mlp_*: the 8-64-64-2 ReLU network in FP32 on the GPU (host pointers; row-major
+ *   X[n][8], Y/T[n][2]); parameter layout W1[64][8] b1[64] W2[64][64] b2[64] W3[2][64]
+ *   b3[2]; loss = sum (y - t)^2 / (2n). oc_mlp_train runs `epochs` full-batch Adam steps
+ *   (beta 0.9 / 0.999, eps 1e-8) in place on params; loss_hist (or NULL) gets the loss
+ *   before each step. These calls need no context. */
+int oc_planner_features(float* out8);
+int oc_autotune_result(double* table, int cap, int* n);
+int oc_planner_load(const float* params, int nparams, const float* feat_mean, const float* feat_std);
+int oc_mlp_nparams(void);
+int oc_mlp_forward(const float* params, const float* X, int n, float* Y);
+int oc_mlp_loss_grad(const float* params, const float* X, const float* T, int n, float* grad, double* loss);
+int oc_mlp_train(float* params, const float* X, const float* T, int n, int epochs, float lr, float* loss_hist);
+
 #ifdef __cplusplus
 }
 #endif

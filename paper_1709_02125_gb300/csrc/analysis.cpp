@@ -46,7 +46,7 @@ uint64_t chain_signature(const std::vector<Loop>& loops, const std::vector<Dat>&
                          uint32_t flags)
 {
     uint64_t h = 1469598103934665603ull;
-    h = mix(h, flags & (OC_FLAG_CYCLIC));
+    h = mix(h, flags & (OC_FLAG_CYCLIC | OC_FLAG_PREFETCH));
     for (const Loop& lp : loops) {
         h = mix(h, (uint64_t)lp.kernel);
         h = mix(h, lp.params.size());
@@ -267,6 +267,31 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
         int S = 1;
         for (int p = 0; p < NP; ++p)
             if (pmax[p] >= pmin[p]) S = std::max(S, pmax[p] - pmin[p] + 1);
+        // Speculative prefetch (Sec. 4.1) uploads the next chain's tile-0 rows while the
+        // last tile runs: pick the smallest S >= the minimum for which the slots of those
+        // rows (hull R0) and of the rows still live in the last two phases (hull LE) do
+        // not meet, so that prefetching never has to wait.
+        if ((flags & OC_FLAG_PREFETCH) && T >= 2 && S < dp.nrows) {
+            int r0a = INT_MAX, r0b = INT_MIN, lea = INT_MAX, leb = INT_MIN;
+            for (int r = 0; r < dp.nrows; ++r) {
+                if (dp.first[r] < 0) continue;
+                if (dp.need_up[r] && dp.first[r] == 0) { r0a = std::min(r0a, r); r0b = std::max(r0b, r + 1); }
+                int pe = dp.dl[r] ? dp.last[r] + 1 : dp.last[r];
+                if (pe >= T - 1) { lea = std::min(lea, r); leb = std::max(leb, r + 1); }
+            }
+            if (r0a < r0b && lea < leb && r0b <= lea) {
+                auto disjoint = [&](int Sc) {
+                    const long long la = lea % Sc, ll = leb - lea, ra = r0a % Sc, rl = r0b - r0a;
+                    if (ll + rl > Sc) return false;
+                    // arcs [la, la + ll) and [ra, ra + rl) on a circle of Sc slots
+                    const long long d1 = ((ra - la) % Sc + Sc) % Sc;  // start of R0 seen from LE
+                    return d1 >= ll && d1 + rl <= Sc;
+                };
+                const int cap = std::min(dp.nrows, S + 2 * (r0b - r0a) + 64);
+                for (int Sc = S; Sc <= cap; ++Sc)
+                    if (disjoint(Sc)) { S = Sc; break; }
+            }
+        }
         dp.S = std::min(S, dp.nrows);
     }
 

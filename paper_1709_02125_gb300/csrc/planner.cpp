@@ -1,14 +1,108 @@
-// Tile planner (placeholder until the autotuner and the MLP are wired in).
+// Tile planner: chain features, the learned (MLP) choice of tile height and pipeline
+// depth, and the candidate grid shared with the exhaustive autotuner (runtime.cu).
+//
+// Features of a chain (inputs of the network, before standardisation):
+//   0 log2(loops)   1 datasets used   2 slow-axis stencil radius   3 bytes per cell
+//   4 budget / footprint   5 dimensions   6 log2(footprint bytes)   7 log2(slow rows)
+// Network outputs: y0 = log2(h / hmax(depth)), y1 = depth; the prediction is snapped to
+// the autotuner grid (nearest fraction in log2, depth rounded to 2..4).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "../../include/oc.h"
+#include "mlp.h"
 #include "planner.h"
 
 namespace oc {
 
-bool planner_choose(const std::vector<Loop>&, const std::vector<Dat>&, const std::vector<int>&, uint32_t,
-                    long long, int, int&, int&)
+const double kGridFrac[kGridN] = {1.0, 0.75, 0.5, 0.375, 0.25, 0.1875, 0.125, 0.0625};
+
+namespace {
+
+struct Learned {
+    bool loaded = false;
+    std::vector<float> params, mean, stdv;
+};
+
+Learned& learned()
 {
-    return false;
+    static Learned L;
+    return L;
 }
 
-void planner_reset() {}
+}  // namespace
+
+void chain_features(const std::vector<Loop>& loops, const std::vector<Dat>& dats, long long budget, float f[8])
+{
+    std::vector<char> used(dats.size(), 0);
+    int radius = 0, nd = 2, Y0 = INT_MAX, Y1 = INT_MIN;
+    for (const Loop& lp : loops) {
+        const int sa = lp.ndim - 1;
+        nd = lp.ndim;
+        Y0 = std::min(Y0, lp.lo[sa]);
+        Y1 = std::max(Y1, lp.hi[sa]);
+        for (const Arg& ar : lp.args) {
+            if (ar.access == OC_REDUCE) continue;
+            used[ar.dat] = 1;
+            radius = std::max(radius, std::max(-ar.rmin[sa], ar.rmax[sa]));
+        }
+    }
+    double nds = 0, bpc = 0, fp = 0;
+    for (size_t d = 0; d < dats.size(); ++d)
+        if (used[d]) {
+            nds += 1;
+            bpc += dats[d].esz;
+            fp += (double)dats[d].bytes();
+        }
+    f[0] = (float)std::log2(std::max<size_t>(1, loops.size()));
+    f[1] = (float)nds;
+    f[2] = (float)radius;
+    f[3] = (float)bpc;
+    f[4] = (float)(fp > 0 ? (double)budget / fp : 1.0);
+    f[5] = (float)nd;
+    f[6] = (float)std::log2(std::max(1.0, fp));
+    f[7] = (float)std::log2((double)std::max(1, Y1 - Y0));
+}
+
+int grid_height(int hmax, int idx) { return std::max(1, (int)std::lround(hmax * kGridFrac[idx])); }
+
+bool planner_load(const float* params, const float* mean, const float* stdv)
+{
+    Learned& L = learned();
+    L.params.assign(params, params + mlp_nparams());
+    L.mean.assign(mean, mean + 8);
+    L.stdv.assign(stdv, stdv + 8);
+    L.loaded = true;
+    return true;
+}
+
+bool planner_loaded() { return learned().loaded; }
+
+bool planner_predict(const float feat[8], int& grid_idx, int& depth)
+{
+    Learned& L = learned();
+    if (!L.loaded) return false;
+    float x[8], y[2];
+    for (int k = 0; k < 8; ++k) x[k] = (feat[k] - L.mean[k]) / (L.stdv[k] > 0 ? L.stdv[k] : 1.0f);
+    if (mlp_forward(L.params.data(), x, 1, y) != cudaSuccess) return false;
+    depth = std::min(4, std::max(2, (int)std::lround(y[1])));
+    int best = 0;
+    double bd = 1e300;
+    for (int i = 0; i < kGridN; ++i) {
+        const double dd = std::fabs(std::log2(kGridFrac[i]) - (double)y[0]);
+        if (dd < bd) { bd = dd; best = i; }
+    }
+    grid_idx = best;
+    return true;
+}
+
+void planner_reset()
+{
+    Learned& L = learned();
+    L = Learned();
+}
 
 }  // namespace oc

@@ -1,5 +1,5 @@
-// Tile planner: chooses (tile height, pipeline depth) for a chain. The exhaustive
-// autotuner and the learned (MLP) predictor live in planner.cpp.
+// Tile planner (planner.cpp): chain features, the candidate grid of (tile height, depth)
+// shared by the exhaustive autotuner and the learned predictor.
 #pragma once
 
 #include <cstdint>
@@ -9,11 +9,15 @@
 
 namespace oc {
 
-// Returns true and sets (h, depth) when the planner has a choice for this chain;
-// false lets the executor fall back to the fixed rule.
-bool planner_choose(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
-                    const std::vector<int>& red_ops, uint32_t flags, long long budget, int mode,
-                    int& h, int& depth);
+constexpr int kGridN = 8;
+extern const double kGridFrac[kGridN];   // tile height as a fraction of the largest fitting one
+
+void chain_features(const std::vector<Loop>& loops, const std::vector<Dat>& dats, long long budget, float f[8]);
+int grid_height(int hmax, int idx);
+bool planner_load(const float* params, const float* mean, const float* stdv);
+bool planner_loaded();
+// Network prediction snapped to the grid; false when no network is loaded.
+bool planner_predict(const float feat[8], int& grid_idx, int& depth);
 void planner_reset();
 
 }  // namespace oc

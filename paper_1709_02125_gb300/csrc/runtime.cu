@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -34,6 +35,7 @@
 #include "launch.h"
 #include "oc_internal.h"
 #include "physics.h"
+#include "mlp.h"
 #include "planner.h"
 
 namespace oc {
@@ -125,6 +127,15 @@ struct Ctx {
     std::vector<TraceRec> tr;
     cudaEvent_t tr_t0 = nullptr;
     std::vector<oc_trace_rec> tr_out;
+    // planner: features of the last planned chain, autotuner table (h, depth, ms, grid
+    // index, largest fitting h) of the last autotuned chain
+    float features[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<std::array<double, 5>> tune;
+    // autotuning trials
+    bool trial = false;
+    cudaEvent_t tm0 = nullptr, tm1 = nullptr;   // timing events of a trial
+    char* trial_sink = nullptr;                 // pinned scratch receiving trial downloads
+    size_t trial_sink_bytes = 0;
 };
 
 static Ctx* g = nullptr;
@@ -187,7 +198,7 @@ static void host_free(void* p, bool pinned)
 // With x0 < x1 (uploads of rows first written over x in [x0, x1)) only the x columns
 // outside [x0, x1) are copied: two strided copies over every x-line of the rows.
 static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cudaStream_t s,
-                     double& bytes, int x0 = 0, int x1 = 0)
+                     double& bytes, int x0 = 0, int x1 = 0, char* host_override = nullptr)
 {
     const long long rb = d.row_bytes();
     const size_t lp = (size_t)d.pitch * d.esz;
@@ -195,7 +206,7 @@ static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cud
         int slot = (int)(((long long)(a - d.y0)) % S);
         int n = std::min(b - a, S - slot);
         char* dev = slab + (long long)slot * rb;
-        char* host = (char*)d.host + (long long)(a - d.y0) * rb;
+        char* host = host_override ? host_override : (char*)d.host + (long long)(a - d.y0) * rb;
         if (x0 < x1) {
             const cudaMemcpyKind kind = up ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
             const size_t lines = (size_t)n * d.ylines;
@@ -353,7 +364,7 @@ static int pool_event(cudaEvent_t& ev, bool persistent)
 static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
                             std::vector<ProfRec>* recs = nullptr, bool persistent = false)
 {
-    const bool prof = (g->flags & OC_FLAG_PROFILE) != 0;
+    const bool prof = (g->flags & OC_FLAG_PROFILE) != 0 && !g->trial;
     for (const LaunchDesc& d : ds) {
         ProfRec pr{};
         if (prof) {
@@ -388,7 +399,7 @@ static int trace_event(cudaEvent_t& ev)
 // Open / close one traced span on stream s (no-ops without OC_FLAG_TRACE).
 static int trace_begin(int tile, int kind, cudaStream_t s)
 {
-    if (!(g->flags & OC_FLAG_TRACE)) return OC_OK;
+    if (!(g->flags & OC_FLAG_TRACE) || g->trial) return OC_OK;
     Ctx::TraceRec r{tile, kind, nullptr, nullptr, 0.0};
     int rc = trace_event(r.a);
     if (!rc) rc = trace_event(r.b);
@@ -400,7 +411,7 @@ static int trace_begin(int tile, int kind, cudaStream_t s)
 
 static int trace_end(cudaStream_t s, double bytes)
 {
-    if (!(g->flags & OC_FLAG_TRACE)) return OC_OK;
+    if (!(g->flags & OC_FLAG_TRACE) || g->trial) return OC_OK;
     g->tr.back().bytes = bytes;
     OC_CUDA(cudaEventRecord(g->tr.back().b, s));
     return OC_OK;
@@ -511,6 +522,45 @@ static bool reads_ghosts(const Plan& P, int di)
 }
 
 // ---------------------------------------------------------------------------------
+static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double* ms_out,
+                    std::chrono::steady_clock::time_point t0);
+
+// Exhaustive autotuner (OC_PLAN_AUTOTUNE): every grid candidate (kGridN tile heights
+// per depth 2..4, heights as fractions of the largest that fits) runs the chain twice as
+// a side-effect-free trial; the faster time counts. The fastest candidate wins.
+static int autotune(const std::vector<Loop>& loops, int& h_best, int& d_best)
+{
+    std::string err;
+    g->tune.clear();
+    double best = 1e300;
+    h_best = 0;
+    for (int depth = 2; depth <= 4; ++depth) {
+        const int hmax = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
+        if (hmax <= 0) continue;
+        int prev = -1;
+        for (int gi = 0; gi < kGridN; ++gi) {
+            const int h = grid_height(hmax, gi);
+            if (h == prev) continue;
+            prev = h;
+            Plan P;
+            build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err);
+            if (P.arena_bytes > g->budget) continue;
+            double ms = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                double m = 0;
+                int rc = run_plan(P, loops, true, &m, std::chrono::steady_clock::now());
+                g->trial = false;
+                if (rc) return rc;
+                ms = std::min(ms, m);
+            }
+            g->descs.erase(P.sig);
+            g->tune.push_back({(double)h, (double)depth, ms, (double)gi, (double)hmax});
+            if (ms < best) { best = ms; h_best = h; d_best = depth; }
+        }
+    }
+    return OC_OK;
+}
+
 static int select_plan_uncached(const std::vector<Loop>& loops, uint64_t csig, Plan*& out)
 {
     std::string err;
@@ -537,11 +587,18 @@ static int select_plan_uncached(const std::vector<Loop>& loops, uint64_t csig, P
     if (g->resident_mode) { int r = leave_resident_mode(); if (r) return r; }
 
     int h = 0, depth = g->force_depth > 0 ? g->force_depth : 3;
-    if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED) {
-        int ph = 0, pd = 0;
-        if (planner_choose(loops, g->dats, g->red_ops, g->flags, g->budget, g->planner_mode, ph, pd)) {
-            h = ph;
-            depth = pd;
+    chain_features(loops, g->dats, g->budget, g->features);
+    if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED && !g->dryrun) {
+        int gi = 0, pd = 3;
+        if (g->planner_mode == OC_PLAN_LEARNED && planner_predict(g->features, gi, pd)) {
+            const int hmax = fit_tile_height(loops, g->dats, g->red_ops, pd, g->flags, g->budget, err);
+            if (hmax > 0) {
+                h = grid_height(hmax, gi);
+                depth = pd;
+            }
+        } else {
+            int rc = autotune(loops, h, depth);
+            if (rc) return rc;
         }
     }
     if (h <= 0) h = g->force_h > 0 ? g->force_h : fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
@@ -633,43 +690,25 @@ static int issue_prefetch(const Plan& P)
     return OC_OK;
 }
 
-static int execute()
+// Run one chain with plan P. In a trial (autotuning) nothing the user can observe
+// changes: downloads land in a scratch buffer, reduction results are dropped, no
+// prefetch, graphs, trace or profile; *ms_out receives the device time of the chain.
+static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double* ms_out,
+                    std::chrono::steady_clock::time_point t0)
 {
-    if (g->queue.empty()) return OC_OK;
-    auto t0 = std::chrono::steady_clock::now();
-    std::vector<Loop> loops;
-    loops.swap(g->queue);
-    Plan* Pp = nullptr;
-    int rc = select_plan(loops, Pp);
-    if (rc) return rc;
-    Plan& P = *Pp;
-    g->last = Pp;
-
-    oc_stats_t& S = g->stats;
-    S.tiles = P.T;
-    S.tile_height = P.h;
-    S.depth = P.depth;
-    S.loops = P.L;
-    S.cell_updates = 0;
-    S.hbm_bytes = 0;
-    S.h2d_bytes = 0;
-    S.d2h_bytes = 0;
-    S.prefetched_bytes = 0;
-    S.graph_replays = 0;
-    S.kernel_launches = 0;
-    for (const Loop& lp : loops) {
-        double pts = (double)lp.points();
-        S.cell_updates += pts;
-        for (const Arg& ar : lp.args)
-            if (ar.access != OC_REDUCE)
-                S.hbm_bytes += pts * g->dats[ar.dat].esz * (ar.access == OC_RW ? 2 : 1);
+    oc_stats_t dummy{};
+    oc_stats_t& S = trial ? dummy : g->stats;
+    g->trial = trial;
+    if (trial) {
+        size_t need = 1;
+        for (const DatPlan& dp : P.dp) need = std::max(need, (size_t)dp.S * (size_t)g->dats[dp.dat].row_bytes());
+        if (need > g->trial_sink_bytes) {
+            host_free(g->trial_sink, true);
+            g->trial_sink = (char*)host_alloc(need, true);
+            if (!g->trial_sink) { g->trial_sink_bytes = 0; return fail(OC_ERR_NOMEM, "pinned trial buffer"); }
+            g->trial_sink_bytes = need;
+        }
     }
-    if (g->dryrun) {
-        S.seconds = 0;
-        S.chains++;
-        return OC_OK;
-    }
-
     auto dit = g->descs.find(P.sig);
     if (dit == g->descs.end()) {
         dit = g->descs.emplace(P.sig, std::vector<std::vector<LaunchDesc>>()).first;
@@ -677,7 +716,7 @@ static int execute()
     }
     const auto& tdesc = dit->second;
     cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
-    rc = ensure_events(std::max(P.T, 1));
+    int rc = ensure_events(std::max(P.T, 1));
     if (rc) return rc;
 
     // parameters of every loop, one block
@@ -701,14 +740,20 @@ static int execute()
         }
     const long long sb = scratch_base(P);
 
-    // a prefetch made for another plan must land before anything else touches slots
-    bool pf_match = g->pf.active && g->pf.sig == P.sig && !P.incore;
+    // a prefetch made for another plan (or before a trial) must land before anything
+    // else touches slots
+    bool pf_match = !trial && g->pf.active && g->pf.sig == P.sig && !P.incore;
     if (g->pf.active) {
         for (int k = 0; k < 3; ++k) OC_CUDA(cudaStreamWaitEvent(g->st[k], g->ev_pf, 0));
         if (!pf_match) g->pf.active = false;
     }
+    if (trial) {
+        OC_CUDA(cudaEventRecord(g->tm0, s0));
+        OC_CUDA(cudaStreamWaitEvent(s1, g->tm0, 0));
+        OC_CUDA(cudaStreamWaitEvent(s2, g->tm0, 0));
+    }
 
-    if (g->flags & OC_FLAG_TRACE) {
+    if (!trial && (g->flags & OC_FLAG_TRACE)) {
         if (!g->tr_t0) OC_CUDA(cudaEventCreate(&g->tr_t0));
         OC_CUDA(cudaEventRecord(g->tr_t0, s0));
         OC_CUDA(cudaStreamWaitEvent(s1, g->tr_t0, 0));
@@ -723,7 +768,7 @@ static int execute()
                                 cudaMemcpyHostToDevice, s0));
     }
 
-    const bool use_graphs = (g->flags & OC_FLAG_GRAPHS) != 0;
+    const bool use_graphs = !trial && (g->flags & OC_FLAG_GRAPHS) != 0;
     GraphSet* gs = nullptr;
     if (use_graphs) {
         gs = &g->graphs[P.sig ^ ((g->flags & OC_FLAG_PROFILE) ? 0xABCDEFull : 0)];
@@ -782,9 +827,10 @@ static int execute()
             if (!rc) rc = trace_end(s0, 0.0);
             if (rc) return rc;
         }
-        for (const Loop& lp : loops)
-            for (const Arg& ar : lp.args)
-                if (ar.access == OC_WRITE || ar.access == OC_RW) g->dats[ar.dat].host_valid = false;
+        if (!trial)
+            for (const Loop& lp : loops)
+                for (const Arg& ar : lp.args)
+                    if (ar.access == OC_WRITE || ar.access == OC_RW) g->dats[ar.dat].host_valid = false;
     } else {
         for (size_t di = 0; di < P.dp.size(); ++di) {
             const Dat& d = g->dats[P.dp[di].dat];
@@ -849,7 +895,8 @@ static int execute()
                     const Dat& d = g->dats[dp.dat];
                     for (const Interval& iv : dp.down)
                         if (iv.t == q) {
-                            rc = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, false, s2, S.d2h_bytes);
+                            rc = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, false, s2, S.d2h_bytes, 0, 0,
+                                           trial ? g->trial_sink : nullptr);
                             if (rc) return rc;
                         }
                 }
@@ -873,9 +920,19 @@ static int execute()
     if (!P.rp.empty())
         OC_CUDA(cudaMemcpyAsync(g->h_results, g->arena + sb + P.results_off, P.rp.size() * 8,
                                 cudaMemcpyDeviceToHost, s0));
-    if (!P.incore && (g->flags & OC_FLAG_PREFETCH)) {
+    if (!trial && !P.incore && (g->flags & OC_FLAG_PREFETCH)) {
         rc = issue_prefetch(P);
         if (rc) return rc;
+    }
+    if (trial) {
+        if (!P.incore && P.T > 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[P.T - 1], 0));
+        OC_CUDA(cudaEventRecord(g->tm1, s0));
+        rc = wait_event(g->tm1, g->timeout_s);
+        if (rc) return rc;
+        float ms = 0;
+        OC_CUDA(cudaEventElapsedTime(&ms, g->tm0, g->tm1));
+        if (ms_out) *ms_out = ms;
+        return OC_OK;
     }
     rc = wait_stream(s0);
     if (rc) return rc;
@@ -905,6 +962,48 @@ static int execute()
     S.chains++;
     return OC_OK;
 }
+
+static int execute()
+{
+    if (g->queue.empty()) return OC_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<Loop> loops;
+    loops.swap(g->queue);
+    Plan* Pp = nullptr;
+    int rc = select_plan(loops, Pp);
+    if (rc) return rc;
+    Plan& P = *Pp;
+    g->last = Pp;
+
+    oc_stats_t& S = g->stats;
+    S.tiles = P.T;
+    S.tile_height = P.h;
+    S.depth = P.depth;
+    S.loops = P.L;
+    S.cell_updates = 0;
+    S.hbm_bytes = 0;
+    S.h2d_bytes = 0;
+    S.d2h_bytes = 0;
+    S.prefetched_bytes = 0;
+    S.graph_replays = 0;
+    S.kernel_launches = 0;
+    for (const Loop& lp : loops) {
+        double pts = (double)lp.points();
+        S.cell_updates += pts;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE)
+                S.hbm_bytes += pts * g->dats[ar.dat].esz * (ar.access == OC_RW ? 2 : 1);
+    }
+    if (g->dryrun) {
+        S.seconds = 0;
+        S.chains++;
+        return OC_OK;
+    }
+    rc = run_plan(P, loops, false, nullptr, t0);
+    g->trial = false;
+    return rc;
+}
+
 
 // ---------------------------------------------------------------------------------
 static bool known_kernel(int k) { return (k >= OC_K_COPY && k <= OC_K_HILO_ADD) || physics_kernel_known(k); }
@@ -1056,6 +1155,8 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         }
         cudaEventCreateWithFlags(&c->ev_pf, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming);
+        cudaEventCreate(&c->tm0);
+        cudaEventCreate(&c->tm1);
     }
     planner_reset();
     return OC_OK;
@@ -1078,6 +1179,9 @@ int oc_finalize(void)
         for (auto e : g->ev_down) cudaEventDestroy(e);
         if (g->ev_pf) cudaEventDestroy(g->ev_pf);
         if (g->ev_end) cudaEventDestroy(g->ev_end);
+        if (g->tm0) cudaEventDestroy(g->tm0);
+        if (g->tm1) cudaEventDestroy(g->tm1);
+        host_free(g->trial_sink, true);
         if (g->own_streams) for (int k = 0; k < 3; ++k) cudaStreamDestroy(g->st[k]);
         if (g->own_arena) cudaFree(g->arena);
     }
@@ -1273,6 +1377,59 @@ int oc_trace(oc_trace_rec* out, int cap, int* n)
     if (!n || (cap > 0 && !out)) return fail(OC_ERR_ARG, "oc_trace: null");
     *n = (int)g->tr_out.size();
     for (int i = 0; i < cap && i < *n; ++i) out[i] = g->tr_out[i];
+    return OC_OK;
+}
+
+int oc_planner_features(float* out8)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_planner_features: no context");
+    if (!out8) return fail(OC_ERR_ARG, "oc_planner_features: null");
+    for (int k = 0; k < 8; ++k) out8[k] = g->features[k];
+    return OC_OK;
+}
+
+int oc_autotune_result(double* table, int cap, int* n)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_autotune_result: no context");
+    if (!n || (cap > 0 && !table)) return fail(OC_ERR_ARG, "oc_autotune_result: null");
+    *n = (int)g->tune.size();
+    for (int i = 0; i < cap && i < *n; ++i)
+        for (int k = 0; k < 5; ++k) table[5 * i + k] = g->tune[i][k];
+    return OC_OK;
+}
+
+int oc_planner_load(const float* params, int nparams, const float* feat_mean, const float* feat_std)
+{
+    if (!params || !feat_mean || !feat_std || nparams != mlp_nparams())
+        return fail(OC_ERR_ARG, "oc_planner_load: expects %d parameters, 8 means and 8 deviations", mlp_nparams());
+    planner_load(params, feat_mean, feat_std);
+    if (g) g->chosen.clear();
+    return OC_OK;
+}
+
+int oc_mlp_nparams(void) { return mlp_nparams(); }
+
+int oc_mlp_forward(const float* params, const float* X, int n, float* Y)
+{
+    if (!params || !X || !Y || n < 1) return fail(OC_ERR_ARG, "oc_mlp_forward: arguments");
+    cudaError_t e = mlp_forward(params, X, n, Y);
+    if (e != cudaSuccess) return fail(OC_ERR_CUDA, "oc_mlp_forward: %s", cudaGetErrorString(e));
+    return OC_OK;
+}
+
+int oc_mlp_loss_grad(const float* params, const float* X, const float* T, int n, float* grad, double* loss)
+{
+    if (!params || !X || !T || !grad || n < 1) return fail(OC_ERR_ARG, "oc_mlp_loss_grad: arguments");
+    cudaError_t e = mlp_loss_grad(params, X, T, n, grad, loss);
+    if (e != cudaSuccess) return fail(OC_ERR_CUDA, "oc_mlp_loss_grad: %s", cudaGetErrorString(e));
+    return OC_OK;
+}
+
+int oc_mlp_train(float* params, const float* X, const float* T, int n, int epochs, float lr, float* loss_hist)
+{
+    if (!params || !X || !T || n < 1 || epochs < 0 || !(lr > 0)) return fail(OC_ERR_ARG, "oc_mlp_train: arguments");
+    cudaError_t e = mlp_train(params, X, T, n, epochs, lr, loss_hist);
+    if (e != cudaSuccess) return fail(OC_ERR_CUDA, "oc_mlp_train: %s", cudaGetErrorString(e));
     return OC_OK;
 }
 

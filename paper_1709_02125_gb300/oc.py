@@ -34,7 +34,8 @@ DTYPES = {"f64": (OC_F64, np.float64), "f32": (OC_F32, np.float32)}
 EXPORTS = ["oc_init", "oc_finalize", "oc_decl_dat", "oc_decl_reduction", "oc_enqueue_loop", "oc_flush",
            "oc_reduce", "oc_fetch_dat", "oc_set_flag", "oc_set_tiling", "oc_stats", "oc_last_error",
            "oc_plan_shape", "oc_plan_ranges", "oc_plan_dat", "oc_kernel_stats", "oc_kernel_stats_reset",
-           "oc_trace"]
+           "oc_trace", "oc_planner_features", "oc_autotune_result", "oc_planner_load", "oc_mlp_nparams",
+           "oc_mlp_forward", "oc_mlp_loss_grad", "oc_mlp_train"]
 
 
 class OcArg(ctypes.Structure):
@@ -98,6 +99,15 @@ def load():
     L.oc_kernel_stats.argtypes = [I, ctypes.POINTER(OcKernelStats)]
     L.oc_kernel_stats_reset.argtypes = []
     L.oc_trace.argtypes = [ctypes.POINTER(OcTraceRec), I, IP]
+    FP = ctypes.POINTER(ctypes.c_float)
+    DP = ctypes.POINTER(ctypes.c_double)
+    L.oc_planner_features.argtypes = [FP]
+    L.oc_autotune_result.argtypes = [DP, I, IP]
+    L.oc_planner_load.argtypes = [FP, I, FP, FP]
+    L.oc_mlp_nparams.argtypes = []
+    L.oc_mlp_forward.argtypes = [FP, FP, I, FP]
+    L.oc_mlp_loss_grad.argtypes = [FP, FP, FP, I, FP, DP]
+    L.oc_mlp_train.argtypes = [FP, FP, FP, I, I, ctypes.c_float, FP]
     for name in EXPORTS:
         if name != "oc_last_error":
             getattr(L, name).restype = I
@@ -242,6 +252,20 @@ class Executor:
         kinds = ("upload", "compute", "download")
         return [(r.tile, kinds[r.kind], r.start_ms, r.end_ms, r.bytes) for r in arr[:n.value]]
 
+    def features(self) -> np.ndarray:
+        f = np.zeros(8, dtype=np.float32)
+        _check(self.L.oc_planner_features(_fp(f)))
+        return f
+
+    def autotune_result(self) -> np.ndarray:
+        """rows (tile height, depth, ms, grid index, hmax) of the last autotuned chain"""
+        n = ctypes.c_int()
+        _check(self.L.oc_autotune_result(None, 0, ctypes.byref(n)))
+        t = np.zeros((max(1, n.value), 5))
+        _check(self.L.oc_autotune_result(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                                         ctypes.byref(n)))
+        return t[:n.value]
+
     def kernel_stats_reset(self):
         _check(self.L.oc_kernel_stats_reset())
 
@@ -291,3 +315,46 @@ def run_chain(ex: Executor, dats, reds, loops, declare: bool = True, flush: bool
         ex.enqueue(lp)
     if flush:
         ex.flush()
+
+
+def _fp(a):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mlp_nparams() -> int:
+    return int(load().oc_mlp_nparams())
+
+
+def mlp_forward(params: np.ndarray, X: np.ndarray) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.zeros((x.shape[0], 2), dtype=np.float32)
+    _check(load().oc_mlp_forward(_fp(p), _fp(x), x.shape[0], _fp(y)))
+    return y
+
+
+def mlp_loss_grad(params: np.ndarray, X: np.ndarray, T: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(T, dtype=np.float32)
+    g = np.zeros_like(p)
+    loss = ctypes.c_double()
+    _check(load().oc_mlp_loss_grad(_fp(p), _fp(x), _fp(t), x.shape[0], _fp(g), ctypes.byref(loss)))
+    return loss.value, g
+
+
+def mlp_train(params: np.ndarray, X: np.ndarray, T: np.ndarray, epochs: int, lr: float):
+    p = np.ascontiguousarray(params, dtype=np.float32).copy()
+    x = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(T, dtype=np.float32)
+    hist = np.zeros(max(1, epochs), dtype=np.float32)
+    _check(load().oc_mlp_train(_fp(p), _fp(x), _fp(t), x.shape[0], int(epochs), float(lr), _fp(hist)))
+    return p, hist[:epochs]
+
+
+def planner_load(params: np.ndarray, mean: np.ndarray, std: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    s = np.ascontiguousarray(std, dtype=np.float32)
+    _check(load().oc_planner_load(_fp(p), p.size, _fp(m), _fp(s)))

@@ -94,12 +94,31 @@ def test_random_chain_repeated_with_prefetch_graphs_cyclic(oracle_lib):
     opt, ro, st = run_gpu(dats, reds, loops, fp // 3, chains=3, flags=flags)
     assert st["graph_replays"] == st["tiles"]
     assert st["prefetched_bytes"] > 0
+    # with the cyclic option, datasets first written in the chain are per-chain
+    # temporaries whose host copies are deliberately not refreshed (Sec. 4.1)
+    temps = _write_first(loops)
+    assert temps
     for d in dats:
-        assert np.array_equal(base[d.name], opt[d.name]), d.name
+        if d.name not in temps:
+            assert np.array_equal(base[d.name], opt[d.name]), d.name
     assert rb == ro
     ref, rref = run_oracle(oracle_lib, dats, reds, loops, chains=3)
     for d in dats:
-        assert rel_max(opt[d.name], ref[d.name]) <= 1e-12, d.name
+        assert rel_max(base[d.name], ref[d.name]) <= 1e-12, d.name
+        if d.name not in temps:
+            assert rel_max(opt[d.name], ref[d.name]) <= 1e-12, d.name
+
+
+def _write_first(loops):
+    first = {}
+    for lp in loops:
+        for a in lp.args:
+            if a.access == "r":
+                first.setdefault(a.name, "r")
+        for a in lp.args:
+            if a.access == "w":
+                first.setdefault(a.name, "w")
+    return {k for k, v in first.items() if v == "w"}
 
 
 def test_random_chain_fp32_storage_error(oracle_lib):

@@ -56,3 +56,40 @@ def build(n: int = 4096, nfields: int = 24, nloops: int = 40, nred: int = 2,
 
 def footprint_bytes(n: int = 4096, nfields: int = 24, esize: int = 8) -> int:
     return nfields * (n + 4) * (n + 4) * esize
+
+
+def build_general(nd: int, n: int, nfields: int, nloops: int, radius: int, seed: int, dtype: str = "f64",
+                  nz: int = None):
+    """Random chain on an n^2 (2-D) or n^2 x nz (3-D) grid with halo `radius`: loops read
+    1-4 other fields at offsets within `radius` on every axis (same recipe as `build`).
+    No initial data (zeros); used for planner sweeps, where values do not matter."""
+    rng = np.random.default_rng(seed)
+    nz = n if nz is None else nz
+    size = (n, n) if nd == 2 else (n, n, nz)
+    lo = (0,) * nd
+    w = 2 * radius + 1
+    loops: List[Loop] = []
+    for _ in range(nloops):
+        out = int(rng.integers(0, nfields))
+        k = int(rng.integers(1, 5))
+        ins = rng.choice([f for f in range(nfields) if f != out], size=min(k, nfields - 1), replace=False)
+        args = [Arg(f"f{out}", WRITE, [(0,) * nd])]
+        for f in ins:
+            npts = int(rng.integers(1, 6))
+            idx = rng.choice(w ** nd, size=min(npts, w ** nd), replace=False)
+            offs = []
+            for i in idx:
+                o, r = [], int(i)
+                for _a in range(nd):
+                    o.append(r % w - radius)
+                    r //= w
+                offs.append(tuple(o))
+            args.append(Arg(f"f{int(f)}", READ, offs))
+        m = sum(len(a.offsets) for a in args[1:])
+        c = rng.uniform(-1.0, 1.0, size=m)
+        c = c * (0.5 / np.abs(c).sum())
+        loops.append(Loop("lincomb", lo, size, args, [0.5] + [float(v) for v in c]))
+    reds = [RedSpec("s0", "sum")]
+    loops.append(Loop("reduce", lo, size, [Arg("f0", READ, [(0,) * nd]), Arg("s0", REDUCE)], [0.0]))
+    dats = [DatSpec(f"f{f}", size, (radius,) * nd, (radius,) * nd, dtype) for f in range(nfields)]
+    return dats, reds, loops
