@@ -302,6 +302,30 @@ int oc_mlp_forward(const float* params, const float* X, int n, float* Y);
 int oc_mlp_loss_grad(const float* params, const float* X, const float* T, int n, float* grad, double* loss);
 int oc_mlp_train(float* params, const float* X, const float* T, int n, int epochs, float lr, float* loss_hist);
 
+/* ---- reduction for callers that cannot allocate ----------------------------------
+ * The paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory (code running inside someone else's CUDA-graph capture, an
+ * allocator-free real-time or safety-critical component, a process whose memory pool
+ * must not grow). It folds a 2-D region of a device array exactly as an OC_K_REDUCE
+ * loop over the same values does (same per-row, per-4096-point partials, same fixed
+ * combine order, so the results are bit-identical), but keeps its scratch -- the
+ * partials -- in one file-scope device array of 65536 doubles (512 KiB) that every GPU
+ * loading the library holds until the process exits. No memory is allocated or freed.
+ *  data      device pointer: rows x row_len elements, consecutive rows row_pitch
+ *            elements apart (row_pitch >= row_len); dtype OC_F64 or OC_F32.
+ *  op        OC_SUM / OC_MAX / OC_MIN; mode 0: value, 1: |value|, 2: value^2.
+ *  out       device pointer to one double receiving the result.
+ *  stream    cudaStream_t (NULL: the legacy default stream). The call only enqueues
+ *            work; synchronise the stream before reading *out.
+ * Requires rows * ceil(row_len / 4096) <= 65536, else OC_ERR_ARG. The first call on a
+ * device (with that device current) looks up the array's device address; make it
+ * before any stream capture. Calls share the array: calls whose work overlaps on the
+ * GPU (e.g. on two streams at once) race and must be ordered by the caller. Errors:
+ * OC_ERR_ARG, OC_ERR_CUDA; the message is in oc_noalloc_last_error(). Needs no context. */
+int oc_reduce_noalloc(const void* data, int dtype, int rows, int row_len, long long row_pitch, int op, int mode,
+                      double* out, void* stream);
+const char* oc_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT_DIR, "liboc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["runtime.cu", "analysis.cpp", "planner.cpp", "physics_host.cpp",
-           "kernels_core.cu", "kernels_physics.cu", "kernels_mlp.cu"]
+           "kernels_core.cu", "kernels_physics.cu", "kernels_mlp.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 
