@@ -125,19 +125,71 @@ def link_bandwidth(torch, nbytes=1 << 30):
     return out
 
 
-def build_workload(dtype: str, n: int):
-    from workloads import random_chain
-    dats, reds, loops = random_chain.build(n=n, dtype=dtype)
-    if dtype == "f32":
-        for d in dats:
-            d.init = d.init.astype(np.float32)
-    fp = random_chain.footprint_bytes(n, 24, 8 if dtype == "f64" else 4)
-    return dats, reds, loops, fp
+def build_workload(name: str, mixed: bool, n: int):
+    """(datasets, reductions, make_step, footprint bytes, cells x timesteps per step).
+    make_step(ex) returns a function running one step (one chain) on executor ex."""
+    if name == "random":
+        from workloads import random_chain
+        dtype = "f32" if mixed else "f64"
+        dats, reds, loops = random_chain.build(n=n, dtype=dtype)
+        if mixed:
+            for d in dats:
+                d.init = d.init.astype(np.float32)
+        fp = random_chain.footprint_bytes(n, 24, 4 if mixed else 8)
+
+        def make_step(ex):
+            def step():
+                for lp in loops:
+                    ex.enqueue(lp)
+                ex.flush()
+                return [ex.reduce(r.name) for r in reds]
+            return step
+        return dats, reds, make_step, fp, 0
+    if name == "euler":
+        from workloads import euler
+        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed)
+        from workloads.spec import RedSpec
+        reds = [RedSpec("dtmin", "min")]
+
+        def make_step(ex):
+            state = {"src": "A", "dst": "B", "dtmin": None}
+
+            def step():
+                if state["dtmin"] is None:
+                    ex.enqueue(euler.dt_loop(n, mixed))
+                    state["dtmin"] = ex.reduce("dtmin")
+                dt = euler.CFL * state["dtmin"]
+                for lp in euler.chain_loops(n, dt, state["src"], state["dst"], mixed):
+                    ex.enqueue(lp)
+                state["dtmin"] = ex.reduce("dtmin")
+                if not mixed:
+                    state["src"], state["dst"] = state["dst"], state["src"]
+                return [state["dtmin"]]
+            return step
+        fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)
+        return dats, reds, make_step, fp, n * n
+    if name == "tgv":
+        from workloads import tgv
+        spc = 1
+        dats = tgv.datasets(n, spc, "f32" if mixed else "f64", tgv.initial(n), mixed)
+        loops = tgv.chain_loops(n, spc, mixed)
+
+        def make_step(ex):
+            def step():
+                for lp in loops:
+                    ex.enqueue(lp)
+                ex.flush()
+                return []
+            return step
+        fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)
+        return dats, [], make_step, fp, n ** 3 * spc
+    raise ValueError(name)
 
 
-def run_variant(torch, name, dtype, budget_frac, flags, planner, steps, warmup, n, dist, profile_kernel=None):
+def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps, warmup, n, dist,
+                profile_kernel=None):
     from paper_1709_02125_gb300 import oc
-    dats, reds, loops, fp = build_workload(dtype, n)
+    dats, reds, make_step, fp, ct = build_workload(workload, mixed, n)
     budget = int(fp * budget_frac)
     streams = [torch.cuda.Stream() for _ in range(3)]
     arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
@@ -148,13 +200,7 @@ def run_variant(torch, name, dtype, budget_frac, flags, planner, steps, warmup, 
             d.init = None  # the library holds its own pinned copy
         for r in reds:
             ex.decl_reduction(r.name, r.op)
-
-        def step():
-            for lp in loops:
-                ex.enqueue(lp)
-            ex.flush()
-            return [ex.reduce(r.name) for r in reds]
-
+        step = make_step(ex)
         for _ in range(warmup):
             step()
         if profile_kernel:
@@ -182,8 +228,9 @@ def run_variant(torch, name, dtype, budget_frac, flags, planner, steps, warmup, 
             dev_s, wall = float(t[0]), float(t[1])
         s1 = ex.stats()
         res = {
-            "dtype": dtype, "budget_bytes": budget, "footprint_bytes": fp,
+            "dtype": "f32" if mixed else "f64", "budget_bytes": budget, "footprint_bytes": fp,
             "cells_per_step": (s1["total_cell_updates"] - s0["total_cell_updates"]) / steps,
+            "cell_steps_per_step": ct,
             "hbm_bytes_per_step": (s1["total_hbm_bytes"] - s0["total_hbm_bytes"]) / steps,
             "h2d_bytes_per_step": (s1["total_h2d_bytes"] - s0["total_h2d_bytes"]) / steps,
             "d2h_bytes_per_step": (s1["total_d2h_bytes"] - s0["total_d2h_bytes"]) / steps,
@@ -199,10 +246,33 @@ def run_variant(torch, name, dtype, budget_frac, flags, planner, steps, warmup, 
         del arena
 
 
+def install_learned_planner(torch):
+    """Train the planner network on the GPU from the committed autotuner sweep and load
+    it; returns a summary (or None when no sweep data is present)."""
+    from paper_1709_02125_gb300 import oc, planner_train
+    path = os.path.join(ROOT, "paper_1709_02125_gb300", "planner_data", "autotune_gb300.jsonl")
+    if not os.path.exists(path):
+        return None
+    rows = planner_train.load_rows(path)
+    k = int(len(rows) * 0.8)
+    t0 = time.perf_counter()
+    p, mean, std, hist = planner_train.train(rows[:k])
+    train_s = time.perf_counter() - t0
+    learned, fixed = planner_train.evaluate(p, mean, std, rows[k:])
+    oc.planner_load(p, mean, std)
+    return {"train_chains": k, "heldout_chains": len(rows) - k, "train_s": round(train_s, 2),
+            "final_loss": float(hist[-1]), "heldout_regret_learned": float(learned.mean()),
+            "heldout_regret_fixed": float(fixed.mean())}
+
+
 def reference_main(args):
     """Time the oracle (plain untiled FP64 C with OpenMP) on the same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return 0
+    if args.workload != "random":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU reference leg times the random-chain "
+                          "workload; the PDE workloads have oracle step functions but no timed leg"}))
         return 0
     import oracle
     from workloads import random_chain
@@ -232,7 +302,7 @@ def reference_main(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_rows_per_step": rows},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": n, "oracle_rows_per_step": rows},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -257,17 +327,31 @@ def cpu_baseline(n, budget_s=20.0):
             "sample": f"{chains} full chains (42 loops, {n}^2 grid, FP64) in {dt:.1f} s"}
 
 
+WORKLOADS = {
+    "random": (WORKLOAD, "lincomb", "k_lincomb<float>", 4096),
+    "euler": ("2-D compressible Euler (MacCormack + 4th-order dissipation), 34 datasets, periodic square, "
+              "CFL min-reduction ends every chain, device budget 1/3 of the footprint", "euler_corr",
+              "k_euler_corr<float>", 15360),
+    "tgv": ("3-D compressible Navier-Stokes Taylor-Green vortex (4th-order central, low-storage RK3), "
+            "27 datasets, one RK3 step per chain, device budget 1/3 of the footprint", "ns_rhs",
+            "k_ns_rhs<float>", 640),
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--workload", default="random", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="grid size (default: the workload's)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore")
+    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore,mixed_incore")
     args = ap.parse_args()
+    desc, prof_kernel, prof_name, n_default = WORKLOADS[args.workload]
+    args.n = args.n or n_default
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
@@ -292,24 +376,30 @@ def main():
     oc.load()
 
     link = link_bandwidth(torch)
+    P, C, G = oc.OC_FLAG_PREFETCH, oc.OC_FLAG_CYCLIC, oc.OC_FLAG_GRAPHS
     variants = {
-        "mixed_learned": ("f32", 1 / 3, oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS, oc.OC_PLAN_LEARNED),
-        "fp64_plain": ("f64", 1 / 3, 0, oc.OC_PLAN_FIXED),
-        "fp64_opt": ("f64", 1 / 3, oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS, oc.OC_PLAN_FIXED),
-        "fp64_incore": ("f64", 1.25, oc.OC_FLAG_GRAPHS, oc.OC_PLAN_FIXED),
+        # name: (mixed, budget / footprint, flags, planner)
+        "mixed_learned": (True, 1 / 3, P | C | G, oc.OC_PLAN_LEARNED),
+        "fp64_plain": (False, 1 / 3, 0, oc.OC_PLAN_FIXED),
+        "fp64_opt": (False, 1 / 3, P | C | G, oc.OC_PLAN_FIXED),
+        "mixed_plain": (True, 1 / 3, 0, oc.OC_PLAN_FIXED),
+        "fp64_incore": (False, 1.25, G, oc.OC_PLAN_FIXED),
+        "mixed_incore": (True, 1.25, G, oc.OC_PLAN_FIXED),
     }
+    planner_info = install_learned_planner(torch) if "mixed_learned" in args.variants else None
     results = {}
     clk = None
     for name in args.variants.split(","):
-        dtype, frac, flags, planner = variants[name]
-        if name == "mixed_learned":
+        mixed, frac, flags, planner = variants[name]
+        if name == args.variants.split(",")[0]:
             with Clocks(local) as clk:
-                results[name] = run_variant(torch, name, dtype, frac, flags, planner, args.steps, args.warmup,
-                                            args.n, dist, profile_kernel="lincomb")
+                results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
+                                            args.warmup, args.n, dist, profile_kernel=prof_kernel)
         else:
-            results[name] = run_variant(torch, name, dtype, frac, flags, planner, args.steps, args.warmup,
-                                        args.n, dist)
-    head = results.get("mixed_learned") or next(iter(results.values()))
+            results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
+                                        args.warmup, args.n, dist)
+    head_name = args.variants.split(",")[0]
+    head = results[head_name]
     N = world
     value = N * head["cells_per_step"] * args.steps / head["device_s"]
     e2e_value = N * head["cells_per_step"] * args.steps / head["wall_s"]
@@ -318,9 +408,10 @@ def main():
     roof = None
     if ks.get("ms"):
         achieved = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_lincomb<float>", "achieved": round(achieved, 1),
-                "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": None, "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
+        roof = {"bound": "hbm", "kernel": prof_name if head["dtype"] == "f32" else prof_name.replace("float", "double"),
+                "achieved": round(achieved, 1), "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "launches": ks["launches"],
+                "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
                 "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"]}
     # binding roofline of the whole pipeline: HBM bytes at peak, link bytes at the link speed
     t_step = head["device_s"] / args.steps
@@ -333,31 +424,37 @@ def main():
         variants_out[k] = {"value": v, "dtype": r["dtype"], "ms_per_step": r["device_s"] / args.steps * 1e3,
                            "tiles": r["tiles"], "tile_height": r["tile_height"], "depth": r["depth"],
                            "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
-                           "budget_bytes": r["budget_bytes"]}
-    if "fp64_plain" in variants_out and "fp64_incore" in variants_out:
-        variants_out["fp64_plain"]["frac_of_incore"] = variants_out["fp64_plain"]["value"] / variants_out["fp64_incore"]["value"]
+                           "budget_bytes": r["budget_bytes"], "footprint_bytes": r["footprint_bytes"]}
+        if r["cell_steps_per_step"]:
+            variants_out[k]["cell_timesteps_per_s"] = N * r["cell_steps_per_step"] * args.steps / r["device_s"]
+    for a, b in (("fp64_plain", "fp64_incore"), ("mixed_learned", "mixed_incore"), ("fp64_opt", "fp64_incore")):
+        if a in variants_out and b in variants_out:
+            variants_out[a]["frac_of_incore"] = variants_out[a]["value"] / variants_out[b]["value"]
     if "mixed_learned" in variants_out and "fp64_plain" in variants_out:
         variants_out["mixed_learned"]["speedup_vs_fp64_plain"] = (variants_out["mixed_learned"]["value"]
                                                                  / variants_out["fp64_plain"]["value"])
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC if args.workload == "random" else f"out-of-core cell-updates/s at 3x mem ({args.workload})",
+        "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["device_s"] / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": head["dtype"] + "+f64-reductions", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": "mixed_learned" if "mixed_learned" in results else args.variants,
+        "vs_baseline": None, "dtype": head["dtype"] + ("+f64-reductions" if head["dtype"] == "f32" else ""),
+        "data": "synthetic",
+        "config": {"workload": desc, "n": args.n, "variant": head_name,
                    "budget_bytes": head["budget_bytes"], "footprint_bytes": head["footprint_bytes"],
                    "tiles": head["tiles"], "tile_height": head["tile_height"], "depth": head["depth"],
-                   "l2": "inputs 3.2 GB (1.6 GB FP32) > 129 MB L2: no flush needed",
+                   "l2": "working set > 129 MB L2 (inputs streamed from host memory): no flush needed",
                    "parallelism": f"replicas x{N}"},
         "roofline": roof,
         "pipeline_roofline": {"t_roof_ms": t_roof * 1e3, "t_ms": t_step * 1e3, "frac": t_roof / t_step,
                               "link": link, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["h2d_bytes_per_step"],
-                "d2h_bytes_per_step": head["d2h_bytes_per_step"] + 16},
+                "d2h_bytes_per_step": head["d2h_bytes_per_step"] + 8 * max(1, len(head["sums"] or []))},
         "gpu_launches": int(head["kernel_launches"]),
         "clocks": clk.summary() if clk else None,
+        "planner": planner_info,
         "variants": variants_out,
     }
-    if rank == 0 and N == 1 and not args.no_cpu_baseline:
+    if rank == 0 and N == 1 and not args.no_cpu_baseline and args.workload == "random":
         line["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(line), flush=True)

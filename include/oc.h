@@ -277,7 +277,7 @@ int oc_plan_ranges(int* se);
 int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
                 int* down, int cap_down, int* ndown);
 
-/* ---- tile planner (spec addition (a); the paper sizes tiles by the fast-memory
+/* ---- tile planner (an addition to the method: the paper sizes tiles by the fast-memory
  * size only, Sec. 4) ----------------------------------------------------------------
  * Features of a chain, 8 floats: log2(loops), datasets used, slow-axis stencil radius,
  * bytes per cell, budget / footprint, dimensions, log2(footprint bytes), log2(slow rows).
@@ -287,8 +287,12 @@ int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
  *   device ms of the chain, grid index (height = round(hmax * {1, 3/4, 1/2, 3/8, 1/4,
  *   3/16, 1/8, 1/16}[index])), hmax (largest fitting height at that depth). *n = rows.
  * oc_planner_load: install the network used by OC_PLAN_LEARNED: oc_mlp_nparams() floats
- *   and the features' standardisation (x - mean) / std. Outputs y0 = log2(h / hmax),
- *   y1 = depth, snapped to the grid. Applies to chains planned afterwards.
+ *   and the features' standardisation (x - mean) / std. The network is a cost model of the
+ *   two main alternatives to the fixed rule (hmax, depth 3): y0 = log2 of the time ratio
+ *   t(hmax, 3) / t(hmax(4), 4), y1 = log2 of t(hmax, 3) / t(3/4 hmax, 3). The planner keeps
+ *   the fixed rule unless max(y0, y1) > 0.03, else takes the alternative with the larger
+ *   predicted gain. Applies to chains planned afterwards, in this and later contexts of
+ *   the process (it needs no context).
  * oc_mlp_*: the 8-64-64-2 ReLU network in FP32 on the GPU (host pointers; row-major
  *   X[n][8], Y/T[n][2]); parameter layout W1[64][8] b1[64] W2[64][64] b2[64] W3[2][64]
  *   b3[2]; loss = sum (y - t)^2 / (2n). oc_mlp_train runs `epochs` full-batch Adam steps

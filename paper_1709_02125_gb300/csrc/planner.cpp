@@ -4,8 +4,12 @@
 // Features of a chain (inputs of the network, before standardisation):
 //   0 log2(loops)   1 datasets used   2 slow-axis stencil radius   3 bytes per cell
 //   4 budget / footprint   5 dimensions   6 log2(footprint bytes)   7 log2(slow rows)
-// Network outputs: y0 = log2(h / hmax(depth)), y1 = depth; the prediction is snapped to
-// the autotuner grid (nearest fraction in log2, depth rounded to 2..4).
+// The network is a cost model of the two alternatives that matter most against the
+// fixed rule (largest fitting height hmax, depth 3): y0 = predicted log2(t(hmax, 3) /
+// t(hmax(4), 4)) and y1 = predicted log2(t(hmax, 3) / t(3/4 hmax, 3)). The planner keeps
+// the fixed rule unless an alternative is predicted to be faster by more than
+// kPlannerMargin;
+// otherwise it takes the alternative with the larger predicted gain.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -88,14 +92,12 @@ bool planner_predict(const float feat[8], int& grid_idx, int& depth)
     float x[8], y[2];
     for (int k = 0; k < 8; ++k) x[k] = (feat[k] - L.mean[k]) / (L.stdv[k] > 0 ? L.stdv[k] : 1.0f);
     if (mlp_forward(L.params.data(), x, 1, y) != cudaSuccess) return false;
-    depth = std::min(4, std::max(2, (int)std::lround(y[1])));
-    int best = 0;
-    double bd = 1e300;
-    for (int i = 0; i < kGridN; ++i) {
-        const double dd = std::fabs(std::log2(kGridFrac[i]) - (double)y[0]);
-        if (dd < bd) { bd = dd; best = i; }
+    grid_idx = 0;
+    depth = 3;
+    if (std::max(y[0], y[1]) > kPlannerMargin) {
+        if (y[0] >= y[1]) depth = 4;
+        else grid_idx = 1;
     }
-    grid_idx = best;
     return true;
 }
 

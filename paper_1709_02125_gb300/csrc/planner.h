@@ -10,13 +10,14 @@
 namespace oc {
 
 constexpr int kGridN = 8;
+constexpr float kPlannerMargin = 0.03f;  // log2 time ratio an alternative must win by
 extern const double kGridFrac[kGridN];   // tile height as a fraction of the largest fitting one
 
 void chain_features(const std::vector<Loop>& loops, const std::vector<Dat>& dats, long long budget, float f[8]);
 int grid_height(int hmax, int idx);
 bool planner_load(const float* params, const float* mean, const float* stdv);
 bool planner_loaded();
-// Network prediction snapped to the grid; false when no network is loaded.
+// The learned choice (grid index, depth); false when no network is loaded.
 bool planner_predict(const float feat[8], int& grid_idx, int& depth);
 void planner_reset();
 

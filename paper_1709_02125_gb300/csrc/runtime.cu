@@ -1158,7 +1158,6 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreate(&c->tm0);
         cudaEventCreate(&c->tm1);
     }
-    planner_reset();
     return OC_OK;
 }
 
@@ -1190,7 +1189,6 @@ int oc_finalize(void)
     host_free(g->h_results, !g->dryrun);
     delete g;
     g = nullptr;
-    planner_reset();
     return OC_OK;
 }
 

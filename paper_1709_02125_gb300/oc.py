@@ -181,7 +181,21 @@ class Executor:
 
     # -- loops --------------------------------------------------------------------
     def enqueue(self, loop, kernel_ids: Optional[Dict[str, int]] = None):
-        """Queue a `workloads.spec.Loop` (names resolved through decl_* handles)."""
+        """Queue a `workloads.spec.Loop` (names resolved through decl_* handles). The
+        marshalled arguments of a Loop object are kept, so enqueueing the same object
+        again (a repeated chain) costs one C call."""
+        key = id(loop)
+        c = self._prepared.get(key) if hasattr(self, "_prepared") else None
+        if c is not None and c[0] is loop and c[1] == tuple(loop.params) and c[2] == (tuple(loop.lo), tuple(loop.hi)):
+            _check(self.L.oc_enqueue_loop(*c[3]))
+            return
+        args = self._marshal(loop, kernel_ids)
+        _check(self.L.oc_enqueue_loop(*args[0]))
+        if not hasattr(self, "_prepared") or len(self._prepared) > 4096:
+            self._prepared = {}
+        self._prepared[key] = (loop, tuple(loop.params), (tuple(loop.lo), tuple(loop.hi)), args[0], args[1])
+
+    def _marshal(self, loop, kernel_ids):
         kid = (kernel_ids or {}).get(loop.kernel, KERNELS.get(loop.kernel))
         if kid is None:
             from . import physics
@@ -205,7 +219,8 @@ class Executor:
             arr[j].npoints = len(a.offsets)
             arr[j].offsets = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         params = (ctypes.c_double * max(1, len(loop.params)))(*[float(p) for p in loop.params])
-        _check(self.L.oc_enqueue_loop(kid, _i3(loop.lo), _i3(loop.hi), n, arr, params, len(loop.params)))
+        call = (kid, _i3(loop.lo), _i3(loop.hi), n, arr, params, len(loop.params))
+        return call, keep
 
     # -- execution / results ----------------------------------------------------------
     def flush(self):
