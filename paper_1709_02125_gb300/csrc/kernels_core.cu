@@ -28,6 +28,12 @@ constexpr int kRows = 4;
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Division of the LINCOMB nonlinear term: IEEE for FP64; for FP32 the fast division
+// (at most 2 ulp), the FP32 form's error budget being far larger.
+__device__ __forceinline__ double nl_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float nl_div(float a, float b) { return __fdividef(a, b); }
+
+
 // One stencil sample m for the R rows of this thread: load, then accumulate.
 template <typename T, int R>
 __device__ __forceinline__ void lincomb_sample(const LaunchDesc& d, const T* cp, int m, int x, int yl,
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ L
             const T a = x0[r];
             const T b = nM > 1 ? x1[r] : x0[r];
             const T c = nM > 2 ? x2[r] : x0[r];
-            acc[r] = acc[r] + ((alpha * a) * b) / (T(1) + c * c);
+            acc[r] = acc[r] + nl_div((alpha * a) * b, T(1) + c * c);
         }
     }
     const DView& o = d.v[0];
@@ -99,6 +105,95 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ L
     for (int r = 0; r < R; ++r) {
         if (s0 + r < shi) ocol[(long long)slot * o.row_elems] = acc[r];
         if (++slot == o.S) slot = 0;
+    }
+}
+
+// Lean LINCOMB: the same samples in the same order as k_lincomb, but every sample's
+// addressing (row base of x = 0, slab slot of the launch's first row) comes precomputed
+// from the host (launch.h SampleRec), so a sample costs a few integer operations per
+// row. Each thread takes one x column and R rows; full row groups skip the row guard.
+template <typename T, int R, int M>
+__global__ void __launch_bounds__(kThreadsX) k_lincomb_lean(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const long long yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int r0 = (int)blockIdx.z * R;
+    const int nr = d.hi[sa] - d.lo[sa] - r0;
+    const T* cp = params_of<T>(d);
+
+    T acc[R], x0[R], x1[R], x2[R];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const SampleRec& sr = d.srec[m];
+        const T c = cp[1 + m];
+        const T* p = reinterpret_cast<const T*>(sr.p0) + yl * sr.pitch + x;
+        int slot = sr.sl0 + r0;
+        if (slot >= sr.S) slot -= sr.S;
+        T val[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int sl = slot + r >= sr.S ? slot + r - sr.S : slot + r;
+            val[r] = (R <= nr || r < nr) ? __ldg(p + (long long)sl * sr.row_elems) : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (m == 0) { acc[r] = c * val[r]; x0[r] = val[r]; }
+            else {
+                acc[r] = fma_t(c, val[r], acc[r]);
+                if (m == 1) x1[r] = val[r];
+                if (m == 2) x2[r] = val[r];
+            }
+        }
+    }
+    const T alpha = cp[0];
+    if (alpha != T(0)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T a = x0[r];
+            const T b = M > 1 ? x1[r] : x0[r];
+            const T c = M > 2 ? x2[r] : x0[r];
+            acc[r] = acc[r] + nl_div((alpha * a) * b, T(1) + c * c);
+        }
+    }
+    const SampleRec& o = d.orec;
+    T* op = const_cast<T*>(reinterpret_cast<const T*>(o.p0)) + yl * o.pitch + x;
+    int slot = o.sl0 + r0;
+    if (slot >= o.S) slot -= o.S;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int sl = slot + r >= o.S ? slot + r - o.S : slot + r;
+        if (R <= nr || r < nr) op[(long long)sl * o.row_elems] = acc[r];
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreadsX) k_copy_lean(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const long long yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int r0 = (int)blockIdx.z * R;
+    const int nr = d.hi[sa] - d.lo[sa] - r0;
+    const SampleRec& sr = d.srec[0];
+    const SampleRec& o = d.orec;
+    const T* p = reinterpret_cast<const T*>(sr.p0) + yl * sr.pitch + x;
+    T* op = const_cast<T*>(reinterpret_cast<const T*>(o.p0)) + yl * o.pitch + x;
+    int si = sr.sl0 + r0, so = o.sl0 + r0;
+    if (si >= sr.S) si -= sr.S;
+    if (so >= o.S) so -= o.S;
+    T val[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int sl = si + r >= sr.S ? si + r - sr.S : si + r;
+        val[r] = (R <= nr || r < nr) ? __ldg(p + (long long)sl * sr.row_elems) : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int sl = so + r >= o.S ? so + r - o.S : so + r;
+        if (R <= nr || r < nr) op[(long long)sl * o.row_elems] = val[r];
     }
 }
 
@@ -225,9 +320,24 @@ cudaError_t launch_pointwise(const LaunchDesc& d, cudaStream_t st, F kern)
     return cudaGetLastError();
 }
 
+constexpr int kLeanRows = 8;
+
+template <typename K>
+cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
+{
+    const int sa = d.ndim - 1;
+    const int nx = d.hi[0] - d.lo[0];
+    const int ns = d.hi[sa] - d.lo[sa];
+    if (nx <= 0 || ns <= 0 || (d.ndim == 3 && d.hi[1] <= d.lo[1])) return cudaSuccess;
+    dim3 grid((nx + kThreadsX - 1) / kThreadsX, d.ndim == 3 ? d.hi[1] - d.lo[1] : 1, (ns + rows - 1) / rows);
+    kern<<<grid, kThreadsX, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
+    if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
     return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
 }
 
@@ -251,6 +361,9 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
     const bool f32 = d.dtype == OC_F32;
     switch (d.kernel) {
     case OC_K_COPY:
+        if (d.lean)
+            return f32 ? launch_rows(d, st, k_copy_lean<float, kLeanRows>, kLeanRows)
+                       : launch_rows(d, st, k_copy_lean<double, kLeanRows>, kLeanRows);
         return f32 ? launch_pointwise(d, st, k_copy<float, kRows>) : launch_pointwise(d, st, k_copy<double, kRows>);
     case OC_K_LINCOMB:
         return f32 ? launch_lincomb<float>(d, st) : launch_lincomb<double>(d, st);

@@ -26,6 +26,17 @@ struct DView {
     int pad_;
 };
 
+// Per-sample addressing precomputed on the host for the lean LINCOMB / COPY kernels:
+// element (x, yl) of the sample's row for launch row r is at
+// p0 + yl * pitch + x + slot * row_elems, slot = sl0 + r (minus S if >= S).
+struct SampleRec {
+    const char* p0;
+    long long row_elems;
+    long long pitch;
+    int S;
+    int sl0;
+};
+
 struct LaunchDesc {
     int kernel;
     int ndim;
@@ -45,6 +56,9 @@ struct LaunchDesc {
     int part_row0;
     int chunks;                // partials per slow row
     int red_op;                // OC_SUM / OC_MAX / OC_MIN
+    int lean;                  // 1: no argument wraps a fast axis; srec / orec are valid
+    SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY
+    SampleRec srec[kLaunchMaxSamples];
 };
 
 // Launch one loop tile on `stream`. Returns cudaSuccess or the launch error.

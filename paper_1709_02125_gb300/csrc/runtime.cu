@@ -326,6 +326,29 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
             }
             if (lp.kernel == OC_K_REDUCE) ns = 0;
             d.nsamp = ns;
+            // lean addressing for LINCOMB / COPY: per-sample base pointers and first slots
+            if ((lp.kernel == OC_K_LINCOMB || lp.kernel == OC_K_COPY) && ns <= kLaunchMaxSamples) {
+                bool wrap = false;
+                for (int j = 0; j < d.nargs; ++j)
+                    if (lp.args[j].access != OC_REDUCE && d.v[j].periodic) wrap = true;
+                if (!wrap) {
+                    const long long esz = d.dtype == OC_F32 ? 4 : 8;
+                    auto rec = [&](const DView& v, int dx, int dy, int ds) {
+                        SampleRec r;
+                        r.p0 = v.base + ((long long)(dy + v.oy) * v.pitch + v.ox + dx) * esz;
+                        r.row_elems = v.row_elems;
+                        r.pitch = v.pitch;
+                        r.S = v.S;
+                        int sl = v.slot0 + (s + ds - v.W0);
+                        r.sl0 = sl >= v.S ? sl - v.S : sl;
+                        return r;
+                    };
+                    d.orec = rec(d.v[0], 0, 0, 0);
+                    for (int m = 0; m < ns; ++m)
+                        d.srec[m] = rec(d.v[d.sarg[m]], d.soff[m][0], lp.ndim == 3 ? d.soff[m][1] : 0, d.soff[m][sa]);
+                    d.lean = 1;
+                }
+            }
             d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
             d.paramsf = (const float*)(g->arena + sb + P.paramsf_off) + P.loop_param[i];
             d.nparams = (int)lp.params.size();
