@@ -339,7 +339,7 @@ WORKLOADS = {
               "CFL min-reduction ends every chain, device budget 1/3 of the footprint", "euler_corr",
               "k_euler_corr<float>", 15360),
     "tgv": ("3-D compressible Navier-Stokes Taylor-Green vortex (4th-order central, low-storage RK3), "
-            "27 datasets, one RK3 step per chain, device budget 1/3 of the footprint", "ns_rhs",
+            "42 datasets, one RK3 step per chain, device budget 1/3 of the footprint", "ns_rhs",
             "k_ns_rhs<float>", 640),
 }
 

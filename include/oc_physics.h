@@ -47,6 +47,14 @@
  *                  dU = A dU + dt R (with W access: dU = dt R, the first low-storage stage).
  * OC_K_NS_UPDATE   [RW U0..U4, R dU0..dU4]                                params [B]
  *                  U = U + B dU.
+ * OC_K_NS_FLUX     [R U0..U4, R u, v, w, p, R the 12 gradients (all at offset 0),
+ *                   W F_{m,a} for m = 0..4, a = x, y, z (15, m-major)]   params [gamma, Ma, Re, Pr]
+ *                  F_{m,a} = flux_{m,a} of OC_K_NS_RHS at the point.
+ * OC_K_NS_DIV      [R F_{m,a} (15, m-major) each at +-1, +-2 along its own axis a,
+ *                   W or RW dU0..dU4]                                    params [hx, hy, hz, A, dt]
+ *                  R_m = - sum over a = x, y, z (in order) of D_a(F_{m,a}); dU as NS_RHS.
+ *                  NS_FLUX followed by NS_DIV computes exactly what NS_RHS computes, with
+ *                  each flux evaluated once per point instead of at four neighbours.
  */
 #ifndef OC_PHYSICS_H
 #define OC_PHYSICS_H
@@ -60,5 +68,7 @@
 #define OC_K_NS_GRAD    21
 #define OC_K_NS_RHS     22
 #define OC_K_NS_UPDATE  23
+#define OC_K_NS_FLUX    24
+#define OC_K_NS_DIV     25
 
 #endif /* OC_PHYSICS_H */

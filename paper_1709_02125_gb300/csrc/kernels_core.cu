@@ -168,6 +168,58 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_lean(const __grid_constan
     }
 }
 
+// LINCOMB for launches whose rows do not cross a slab end (the common case: a slab
+// wraps once per S rows): a row is one 32-bit multiply-add away from the sample's base.
+template <typename T, int R, int M>
+__global__ void __launch_bounds__(kThreadsX) k_lincomb_nowrap(const __grid_constant__ LaunchDesc d)
+{
+    const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const int sa = d.ndim - 1;
+    const long long yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
+    const int r0 = (int)blockIdx.z * R;
+    const int nr = d.hi[sa] - d.lo[sa] - r0;
+    const T* cp = params_of<T>(d);
+
+    T acc[R], x0[R], x1[R], x2[R];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const SampleRec& sr = d.srec[m];
+        const int re = d.sre[m];
+        const T c = cp[1 + m];
+        const T* p = reinterpret_cast<const T*>(sr.p0) + yl * sr.pitch + x;
+        const int o = (sr.sl0 + r0) * re;
+        T val[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) val[r] = (R <= nr || r < nr) ? __ldg(p + (o + r * re)) : T(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (m == 0) { acc[r] = c * val[r]; x0[r] = val[r]; }
+            else {
+                acc[r] = fma_t(c, val[r], acc[r]);
+                if (m == 1) x1[r] = val[r];
+                if (m == 2) x2[r] = val[r];
+            }
+        }
+    }
+    const T alpha = cp[0];
+    if (alpha != T(0)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T a = x0[r];
+            const T b = M > 1 ? x1[r] : x0[r];
+            const T c = M > 2 ? x2[r] : x0[r];
+            acc[r] = acc[r] + nl_div((alpha * a) * b, T(1) + c * c);
+        }
+    }
+    const SampleRec& od = d.orec;
+    T* op = const_cast<T*>(reinterpret_cast<const T*>(od.p0)) + yl * od.pitch + x;
+    const int oo = (od.sl0 + r0) * d.ore;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (R <= nr || r < nr) op[oo + r * d.ore] = acc[r];
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreadsX) k_copy_lean(const __grid_constant__ LaunchDesc d)
 {
@@ -337,6 +389,7 @@ cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
+    if (d.nowrap) return launch_rows(d, st, k_lincomb_nowrap<T, kLeanRows, M>, kLeanRows);
     if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
     return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
 }

@@ -245,6 +245,49 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_rhs(const __grid_constant__ La
     }
 }
 
+// The 15 fluxes of the point (same evaluation as the fused kernel's ns_fluxes).
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX) k_ns_flux(const __grid_constant__ LaunchDesc d)
+{
+    Pt p;
+    if (!point_of(d, p)) return;
+    const T* pd = params_of<T>(d);
+    const T gamma = pd[0], Ma = pd[1], Re = pd[2], Pr = pd[3];
+    const T mu = Re > T(0) ? T(1) / Re : T(0);
+    const T kc = mu / ((((gamma - T(1)) * Ma) * Ma) * Pr);
+#pragma unroll 1
+    for (int a = 0; a < 3; ++a) {
+        T f[5];
+        ns_fluxes<T>(d, p, a, mu, kc, f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) S<T>(d, 21 + 3 * m + a, p, f[m]);
+    }
+}
+
+// R_m = - sum_a D_a(F_{m,a}) from stored fluxes, then the low-storage RK register.
+template <typename T>
+__global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ LaunchDesc d)
+{
+    Pt p;
+    if (!point_of(d, p)) return;
+    const T* pd = params_of<T>(d);
+    const T A = pd[3], dt = pd[4];
+    const bool rw = d.access[15] == OC_RW;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        T r = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int arg = 3 * m + a;
+            const T fm2 = L<T>(d, arg, shift(d, p, a, -2)), fm1 = L<T>(d, arg, shift(d, p, a, -1));
+            const T fp1 = L<T>(d, arg, shift(d, p, a, 1)), fp2 = L<T>(d, arg, shift(d, p, a, 2));
+            r = r - ((fm2 - T(8) * fm1) + (T(8) * fp1 - fp2)) / (T(12) * pd[a]);
+        }
+        const T du = rw ? A * L<T>(d, 15 + m, p) + dt * r : dt * r;
+        S<T>(d, 15 + m, p, du);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsX) k_ns_update(const __grid_constant__ LaunchDesc d)
 {
@@ -289,6 +332,8 @@ cudaError_t launch_physics(const LaunchDesc& d, cudaStream_t st)
     case OC_K_NS_GRAD: return f ? launch_pt(d, st, k_ns_grad<float>) : launch_pt(d, st, k_ns_grad<double>);
     case OC_K_NS_RHS: return f ? launch_pt(d, st, k_ns_rhs<float>) : launch_pt(d, st, k_ns_rhs<double>);
     case OC_K_NS_UPDATE: return f ? launch_pt(d, st, k_ns_update<float>) : launch_pt(d, st, k_ns_update<double>);
+    case OC_K_NS_FLUX: return f ? launch_pt(d, st, k_ns_flux<float>) : launch_pt(d, st, k_ns_flux<double>);
+    case OC_K_NS_DIV: return f ? launch_pt(d, st, k_ns_div<float>) : launch_pt(d, st, k_ns_div<double>);
     default: return cudaErrorInvalidValue;
     }
 }

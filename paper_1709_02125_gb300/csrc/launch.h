@@ -7,7 +7,7 @@
 
 namespace oc {
 
-constexpr int kLaunchMaxArgs = 32;
+constexpr int kLaunchMaxArgs = 40;
 constexpr int kLaunchMaxSamples = 64;
 
 // Device view of one dataset argument inside one launch. A slow row s lives at
@@ -57,6 +57,9 @@ struct LaunchDesc {
     int chunks;                // partials per slow row
     int red_op;                // OC_SUM / OC_MAX / OC_MIN
     int lean;                  // 1: no argument wraps a fast axis; srec / orec are valid
+    int nowrap;                // 1: no slab wrap inside this launch's rows, 32-bit offsets fit
+    int ore;                   // output row stride in elements (nowrap launches)
+    int sre[kLaunchMaxSamples];// sample row strides in elements (nowrap launches)
     SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY
     SampleRec srec[kLaunchMaxSamples];
 };

@@ -10,7 +10,7 @@
 
 namespace oc {
 
-constexpr int kMaxArgs = 32;
+constexpr int kMaxArgs = 40;
 constexpr int kMaxSamples = 64;
 
 // A dataset (arXiv 1709.02125, Sec. 3) with the library-owned host store.

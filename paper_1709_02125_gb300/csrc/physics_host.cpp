@@ -81,6 +81,21 @@ bool layout(int k, int nargs, std::vector<ArgSpec>& a, int& ndim, int& nparams, 
         add(a, 5, -1, kP0);
         return true;
     case OC_K_NS_UPDATE: ndim = 3; nparams = 1; add(a, 5, OC_RW, kP0); add(a, 5, OC_READ, kP0); return true;
+    case OC_K_NS_FLUX: ndim = 3; nparams = 4; add(a, 21, OC_READ, kP0); add(a, 15, OC_WRITE, kP0); return true;
+    case OC_K_NS_DIV:
+        ndim = 3; nparams = 5;
+        for (int m = 0; m < 5; ++m)
+            for (int ax = 0; ax < 3; ++ax) {
+                Stencil st;
+                for (int k : {-2, -1, 1, 2}) {
+                    Off o = {0, 0, 0};
+                    o[ax] = k;
+                    st.push_back(o);
+                }
+                add(a, 1, OC_READ, st);
+            }
+        add(a, 5, -1, kP0);
+        return true;
     default: return false;
     }
 }
@@ -146,9 +161,10 @@ bool physics_validate(const Loop& lp, const std::vector<Dat>&, std::string& msg)
         msg = "kernel " + std::to_string(lp.kernel) + ": last argument must be a reduction";
         return false;
     }
-    if (lp.kernel == OC_K_NS_RHS) {
-        const int acc0 = lp.args[21].access;
-        for (int j = 22; j < 26; ++j)
+    if (lp.kernel == OC_K_NS_RHS || lp.kernel == OC_K_NS_DIV) {
+        const int first = lp.kernel == OC_K_NS_RHS ? 21 : 15;
+        const int acc0 = lp.args[first].access;
+        for (int j = first + 1; j < first + 5; ++j)
             if (lp.args[j].access != acc0) {
                 msg = "NS_RHS: the five dU arguments share one access mode";
                 return false;

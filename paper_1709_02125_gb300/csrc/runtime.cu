@@ -76,6 +76,23 @@ struct GraphSet {
     std::vector<std::vector<ProfRec>> prof;  // events captured into each tile's graph
 };
 
+// The whole pipeline of one chain shape (parameter upload, every tile's uploads,
+// kernels and downloads on the three streams with their dependencies, the reduction
+// combine, the result read-back and the speculative prefetch) captured once as one
+// CUDA graph, with what the capture counted.
+struct ChainGraph {
+    cudaGraphExec_t exec = nullptr;
+    double h2d = 0, d2h = 0, prefetched = 0;
+    int launches = 0;
+    bool pf_active = false;
+    uint64_t pf_sig = 0;
+    double pf_bytes = 0;
+    std::vector<std::vector<Interval>> pf_rows;
+    // pinned parameter / result staging the graph's copy nodes point at (owned)
+    double* hp = nullptr;
+    double* hr = nullptr;
+};
+
 struct Prefetch {
     bool active = false;
     uint64_t sig = 0;
@@ -102,6 +119,8 @@ struct Ctx {
     std::unordered_map<uint64_t, Plan*> chosen;      // chain shape + settings -> plan
     std::unordered_map<uint64_t, std::vector<std::vector<LaunchDesc>>> descs;  // plan sig -> tiles
     std::unordered_map<uint64_t, GraphSet> graphs;
+    std::unordered_map<uint64_t, ChainGraph> chain_graphs;
+    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
     int force_h = 0, force_depth = 0;
     std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
@@ -347,6 +366,19 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                     for (int m = 0; m < ns; ++m)
                         d.srec[m] = rec(d.v[d.sarg[m]], d.soff[m][0], lp.ndim == 3 ? d.soff[m][1] : 0, d.soff[m][sa]);
                     d.lean = 1;
+                    // no slab wrap across this launch's rows and 32-bit element offsets:
+                    // the kernels then address a row with one multiply-add
+                    const long long rows = e - s;
+                    auto fits = [&](const SampleRec& r) {
+                        return r.sl0 + rows <= r.S && (long long)r.S * r.row_elems < (1LL << 31);
+                    };
+                    bool nw = fits(d.orec);
+                    for (int m = 0; m < ns && nw; ++m) nw = fits(d.srec[m]);
+                    if (nw) {
+                        d.nowrap = 1;
+                        d.ore = (int)d.orec.row_elems;
+                        for (int m = 0; m < ns; ++m) d.sre[m] = (int)d.srec[m].row_elems;
+                    }
                 }
             }
             d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
@@ -713,6 +745,11 @@ static int issue_prefetch(const Plan& P)
     return OC_OK;
 }
 
+static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool capturing, bool pf_match,
+                       oc_stats_t& S, long long sb, const double* hp, const float* hpf, double* hr);
+static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool graphed, double* ms_out,
+                        oc_stats_t& S, std::chrono::steady_clock::time_point t0, const double* hr);
+
 // Run one chain with plan P. In a trial (autotuning) nothing the user can observe
 // changes: downloads land in a scratch buffer, reduction results are dropped, no
 // prefetch, graphs, trace or profile; *ms_out receives the device time of the chain.
@@ -737,7 +774,7 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         dit = g->descs.emplace(P.sig, std::vector<std::vector<LaunchDesc>>()).first;
         build_descs(P, loops, dit->second);
     }
-    const auto& tdesc = dit->second;
+    (void)dit;
     cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
     int rc = ensure_events(std::max(P.T, 1));
     if (rc) return rc;
@@ -784,14 +821,126 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         g->tr.clear();
         g->tr_next = 0;
     }
+    // the chain's upload and download streams start after all earlier work of stream 0
+    // (the previous chain's whole-chain graph included)
+    OC_CUDA(cudaEventRecord(g->ev_fork, s0));
+    OC_CUDA(cudaStreamWaitEvent(s1, g->ev_fork, 0));
+    OC_CUDA(cudaStreamWaitEvent(s2, g->ev_fork, 0));
+    bool incore_uploads = false;
+    if (P.incore)
+        for (const DatPlan& dp : P.dp) incore_uploads = incore_uploads || !g->dats[dp.dat].dev_valid;
+    const bool chain_graph = !trial && (g->flags & OC_FLAG_GRAPHS) && !(g->flags & (OC_FLAG_TRACE | OC_FLAG_PROFILE)) &&
+                             !incore_uploads;
+    ChainGraph* cg = nullptr;
+    bool replay = false;
+    if (chain_graph) {
+        const uint64_t key = P.sig ^ (pf_match ? 0x9E3779B1ull : 0) ^ ((g->flags & OC_FLAG_PREFETCH) ? (0x7F4A7C15ull << 20) : 0);
+        cg = &g->chain_graphs[key];
+        replay = cg->exec != nullptr;
+    }
+    // staging of parameters and results: the context's buffers, or the graph's own (a
+    // captured copy node keeps its host address for the graph's lifetime); pinned host
+    // memory cannot be allocated while a stream is being captured
+    const double* hp = g->h_params;
+    const float* hpf = h_paramsf;
+    double* hr = g->h_results;
+    if (chain_graph) {
+        if (!cg->hp) {
+            cg->hp = (double*)host_alloc((size_t)std::max(1, P.nparams) * 12, true);
+            cg->hr = (double*)host_alloc(std::max<size_t>(1, P.rp.size()) * 8, true);
+            if (!cg->hp || !cg->hr) return fail(OC_ERR_NOMEM, "pinned graph staging");
+        }
+        memcpy(cg->hp, g->h_params, (size_t)P.nparams * 8);
+        memcpy(cg->hp + std::max(1, P.nparams), h_paramsf, (size_t)P.nparams * 4);
+        hp = cg->hp;
+        hpf = (const float*)(cg->hp + std::max(1, P.nparams));
+        hr = cg->hr;
+        if (!replay) {
+            OC_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e1 = cudaEventRecord(g->ev_fork2, s0);
+            cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s1, g->ev_fork2, 0) : e1;
+            cudaError_t e3 = e2 == cudaSuccess ? cudaStreamWaitEvent(s2, g->ev_fork2, 0) : e2;
+            if (e3 != cudaSuccess) {
+                cudaGraph_t tmp;
+                cudaStreamEndCapture(s0, &tmp);
+                if (tmp) cudaGraphDestroy(tmp);
+                return fail(OC_ERR_CUDA, "chain capture failed: %s", cudaGetErrorString(e3));
+            }
+        }
+    }
+    if (!replay) {
+        rc = issue_chain(P, loops, trial, chain_graph, pf_match, S, sb, hp, hpf, hr);
+        if (chain_graph) {
+            cudaError_t e = cudaSuccess;
+            if (!rc) {
+                e = cudaEventRecord(g->ev_j1, s1);
+                if (e == cudaSuccess) e = cudaEventRecord(g->ev_j2, s2);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j1, 0);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j2, 0);
+            }
+            cudaGraph_t gr = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s0, &gr);
+            if (rc || e != cudaSuccess || ce != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                if (rc) return rc;
+                return fail(OC_ERR_CUDA, "chain capture failed: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : ce));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&cg->exec, gr, 0);
+            cudaGraphDestroy(gr);
+            if (ie != cudaSuccess) return fail(OC_ERR_CUDA, "chain graph instantiation failed: %s", cudaGetErrorString(ie));
+            cg->h2d = S.h2d_bytes;
+            cg->d2h = S.d2h_bytes;
+            cg->prefetched = S.prefetched_bytes;
+            cg->launches = S.kernel_launches;
+            cg->pf_active = g->pf.active;
+            cg->pf_sig = g->pf.sig;
+            cg->pf_bytes = g->pf.bytes;
+            cg->pf_rows = g->pf.rows;
+        } else if (rc) {
+            return rc;
+        }
+    } else {
+        S.h2d_bytes = cg->h2d;
+        S.d2h_bytes = cg->d2h;
+        S.prefetched_bytes = cg->prefetched;
+        S.kernel_launches = cg->launches;
+        S.graph_replays = P.T;
+        g->pf.active = cg->pf_active;
+        g->pf.sig = cg->pf_sig;
+        g->pf.bytes = cg->pf_bytes;
+        g->pf.rows = cg->pf_rows;
+        if (!P.incore)
+            for (size_t di = 0; di < P.dp.size(); ++di) {
+                const Dat& d = g->dats[P.dp[di].dat];
+                if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+            }
+    }
+    if (chain_graph) {
+        OC_CUDA(cudaGraphLaunch(cg->exec, s0));
+        // the prefetch event recorded inside the capture is a graph node; the next chain
+        // waits on a real event, which the graph's end (it joins the copy streams) covers
+        if (g->pf.active) OC_CUDA(cudaEventRecord(g->ev_pf, s0));
+    }
+    return finish_chain(P, loops, trial, chain_graph, ms_out, S, t0, hr);
+}
+
+// Issue every asynchronous operation of one chain on the three streams (optionally
+// inside a stream capture: then no per-tile graphs, trace or profile).
+static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool capturing, bool pf_match,
+                       oc_stats_t& S, long long sb, const double* hp, const float* hpf, double* hr)
+{
+    cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
+    int rc = OC_OK;
+    const auto& tdesc = g->descs[P.sig];
     if (P.nparams > 0) {
-        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.params_off, g->h_params, (size_t)P.nparams * 8,
+        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.params_off, hp, (size_t)P.nparams * 8,
                                 cudaMemcpyHostToDevice, s0));
-        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.paramsf_off, h_paramsf, (size_t)P.nparams * 4,
+        OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.paramsf_off, hpf, (size_t)P.nparams * 4,
                                 cudaMemcpyHostToDevice, s0));
     }
 
-    const bool use_graphs = !trial && (g->flags & OC_FLAG_GRAPHS) != 0;
+    const bool use_graphs = !trial && !capturing && (g->flags & OC_FLAG_GRAPHS) != 0;
     GraphSet* gs = nullptr;
     if (use_graphs) {
         gs = &g->graphs[P.sig ^ ((g->flags & OC_FLAG_PROFILE) ? 0xABCDEFull : 0)];
@@ -941,12 +1090,22 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         S.kernel_launches++;
     }
     if (!P.rp.empty())
-        OC_CUDA(cudaMemcpyAsync(g->h_results, g->arena + sb + P.results_off, P.rp.size() * 8,
+        OC_CUDA(cudaMemcpyAsync(hr, g->arena + sb + P.results_off, P.rp.size() * 8,
                                 cudaMemcpyDeviceToHost, s0));
     if (!trial && !P.incore && (g->flags & OC_FLAG_PREFETCH)) {
         rc = issue_prefetch(P);
         if (rc) return rc;
     }
+    return OC_OK;
+}
+
+// Wait for a chain issued by run_plan and publish its results and counters.
+static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool graphed, double* ms_out,
+                        oc_stats_t& S, std::chrono::steady_clock::time_point t0, const double* hr)
+{
+    cudaStream_t s0 = g->st[0];
+    int rc = OC_OK;
+    (void)loops;
     if (trial) {
         if (!P.incore && P.T > 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[P.T - 1], 0));
         OC_CUDA(cudaEventRecord(g->tm1, s0));
@@ -959,12 +1118,12 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     }
     rc = wait_stream(s0);
     if (rc) return rc;
-    if (!P.incore && P.T > 0) {
+    if (!graphed && !P.incore && P.T > 0) {
         rc = wait_event(g->ev_down[P.T - 1], g->timeout_s);
         if (rc) return rc;
     }
     for (size_t r = 0; r < P.rp.size(); ++r) {
-        g->red_val[P.rp[r].handle] = g->h_results[r];
+        g->red_val[P.rp[r].handle] = hr[r];
         g->red_has[P.rp[r].handle] = 1;
     }
     if (!g->prof_pending.empty()) {
@@ -1180,6 +1339,10 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming);
         cudaEventCreate(&c->tm0);
         cudaEventCreate(&c->tm1);
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_j1, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_j2, cudaEventDisableTiming);
     }
     return OC_OK;
 }
@@ -1201,6 +1364,12 @@ int oc_finalize(void)
         for (auto e : g->ev_down) cudaEventDestroy(e);
         if (g->ev_pf) cudaEventDestroy(g->ev_pf);
         if (g->ev_end) cudaEventDestroy(g->ev_end);
+        for (auto& kv : g->chain_graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            host_free(kv.second.hp, true);
+            host_free(kv.second.hr, true);
+        }
+        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2}) if (e) cudaEventDestroy(e);
         if (g->tm0) cudaEventDestroy(g->tm0);
         if (g->tm1) cudaEventDestroy(g->tm1);
         host_free(g->trial_sink, true);

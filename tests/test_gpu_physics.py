@@ -91,12 +91,12 @@ def test_euler_mixed_error_and_totals(oracle_lib):
     assert np.allclose(dtm, dto, rtol=1e-5, atol=0)
 
 
-def tgv_gpu(n, chains, spc, budget, mixed=False, h=0, flags=0):
+def tgv_gpu(n, chains, spc, budget, mixed=False, h=0, flags=0, fused=False):
     from paper_1709_02125_gb300 import oc
     G = tgv.ghost(spc)
     with oc.Executor(budget, flags=flags) as ex:
         ex.set_tiling(h, 3 if h else 0)
-        tgv.run(ex, n, chains, spc, mixed=mixed)
+        tgv.run(ex, n, chains, spc, mixed=mixed, fused=fused)
         st = ex.stats()
         U = np.stack([ex.fetch(c)[G:G + n].astype(np.float64) for c in tgv.CONS])
         if mixed:
@@ -113,12 +113,12 @@ def tgv_oracle(n, steps):
     return U
 
 
-@pytest.mark.parametrize("spc", [1, 2])
-def test_tgv_fp64_tiled_untiled_oracle(oracle_lib, spc):
+@pytest.mark.parametrize("spc,fused", [(1, False), (2, False), (1, True)])
+def test_tgv_fp64_tiled_untiled_oracle(oracle_lib, spc, fused):
     n, chains = 24, 2
-    fp = footprint(tgv.datasets(n, spc))
-    Ui, sti = tgv_gpu(n, chains, spc, 4 * fp)
-    Ut, stt = tgv_gpu(n, chains, spc, 4 * fp, h=7)
+    fp = footprint(tgv.datasets(n, spc, fused=fused))
+    Ui, sti = tgv_gpu(n, chains, spc, 4 * fp, fused=fused)
+    Ut, stt = tgv_gpu(n, chains, spc, 4 * fp, h=7, fused=fused)
     assert sti["tiles"] == 1 and stt["tiles"] > 1
     assert np.array_equal(Ui, Ut)
     Uo = tgv_oracle(n, chains * spc)

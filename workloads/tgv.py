@@ -10,9 +10,10 @@ paper's OpenSBLI runs).
 
 `chain_loops` is the user code of `steps` time steps (3 low-storage RK3 stages each)
 as one loop chain for the executor. Datasets: the 5 conserved variables, the 5 RK
-registers, 5 primitives (u, v, w, p, T) and 12 gradients (d{u,v,w,T}/d{x,y,z}) --
-27 in all. Per stage: NS_PRIM, NS_GRAD, NS_RHS (dU = A dU + dt R), NS_UPDATE
-(U += B dU). x and y are periodic inside each z-plane; z, the tiled axis, is periodic
+registers, 5 primitives (u, v, w, p, T), 12 gradients (d{u,v,w,T}/d{x,y,z}) and 15
+fluxes -- 42 in all (27 with the fused residual kernel). Per stage: NS_PRIM, NS_GRAD, NS_FLUX (the 15 fluxes, 15 more
+temporaries), NS_DIV (dU = A dU + dt R), NS_UPDATE (U += B dU); or, fused, NS_RHS in
+place of NS_FLUX + NS_DIV. x and y are periodic inside each z-plane; z, the tiled axis, is periodic
 through deep ghost planes (4 per stage) into which earlier loops extend their ranges.
 """
 from __future__ import annotations
@@ -30,6 +31,7 @@ REACH_PER_STAGE = 4
 CONS = ["rho", "ru", "rv", "rw", "rE"]
 PRIM = ["u", "v", "w", "p", "T"]
 GRADS = [f"d{f}d{a}" for f in ("u", "v", "w", "T") for a in ("x", "y", "z")]
+FLUXES = [f"F{m}{a}" for m in range(5) for a in ("x", "y", "z")]   # flux of component m along a
 
 
 def h_of(n: int) -> float:
@@ -59,7 +61,7 @@ def ghost(steps: int) -> int:
 
 
 def datasets(n: int, steps: int = 1, dtype: str = "f64", U0: np.ndarray = None,
-             mixed: bool = False) -> List[DatSpec]:
+             mixed: bool = False, fused: bool = False) -> List[DatSpec]:
     G = ghost(steps)
     per = (0, 1, 2)
     ds = []
@@ -84,6 +86,9 @@ def datasets(n: int, steps: int = 1, dtype: str = "f64", U0: np.ndarray = None,
         dat(c, G)
     for c in GRADS:
         dat(c, G - 2)
+    if not fused:
+        for c in FLUXES:
+            dat(c, G - 2)
     return ds
 
 
@@ -91,8 +96,9 @@ STAR = [(0, 0, 0)] + [tuple(d * s if a == b else 0 for b in range(3)) for a in r
                       for d in (-1, 1)]
 
 
-def chain_loops(n: int, steps: int = 1, mixed: bool = False, re: float = RE) -> List[Loop]:
-    """`steps` RK3 steps as one chain (ranges shrink towards the last stage)."""
+def chain_loops(n: int, steps: int = 1, mixed: bool = False, re: float = RE, fused: bool = False) -> List[Loop]:
+    """`steps` RK3 steps as one chain (ranges shrink towards the last stage). fused: one
+    NS_RHS loop per stage instead of NS_FLUX + NS_DIV."""
     G = ghost(steps)
     h = h_of(n)
     dt = dt_of(n)
@@ -108,13 +114,24 @@ def chain_loops(n: int, steps: int = 1, mixed: bool = False, re: float = RE) -> 
         lo, hi = full(-ext - 2, n + ext + 2)
         loops.append(Loop("ns_grad", lo, hi, [Arg(c, READ, STAR[1:]) for c in ("u", "v", "w", "T")] +
                           [Arg(c, WRITE) for c in GRADS], [h, h, h]))
-        lo, hi = full(-ext, n + ext)
         acc = WRITE if s == 0 else RW
-        loops.append(Loop("ns_rhs", lo, hi, [Arg(c, READ, STAR[1:]) for c in CONS] +
-                          [Arg(c, READ, STAR[1:]) for c in ("u", "v", "w", "p")] +
-                          [Arg(c, READ, STAR[1:]) for c in GRADS] +
-                          [Arg("d" + c, acc) for c in CONS],
-                          [GAMMA, MA, re, PR, h, h, h, RK_A[s], dt]))
+        if fused:
+            lo, hi = full(-ext, n + ext)
+            loops.append(Loop("ns_rhs", lo, hi, [Arg(c, READ, STAR[1:]) for c in CONS] +
+                              [Arg(c, READ, STAR[1:]) for c in ("u", "v", "w", "p")] +
+                              [Arg(c, READ, STAR[1:]) for c in GRADS] +
+                              [Arg("d" + c, acc) for c in CONS],
+                              [GAMMA, MA, re, PR, h, h, h, RK_A[s], dt]))
+        else:
+            loops.append(Loop("ns_flux", lo, hi, [Arg(c, READ, STAR[:1]) for c in CONS] +
+                              [Arg(c, READ, STAR[:1]) for c in ("u", "v", "w", "p")] +
+                              [Arg(c, READ, STAR[:1]) for c in GRADS] +
+                              [Arg(c, WRITE, STAR[:1]) for c in FLUXES], [GAMMA, MA, re, PR]))
+            lo, hi = full(-ext, n + ext)
+            along = [STAR[1:5], STAR[5:9], STAR[9:13]]   # +-1, +-2 along x, y, z
+            loops.append(Loop("ns_div", lo, hi, [Arg(FLUXES[3 * m + a], READ, along[a])
+                                                 for m in range(5) for a in range(3)] +
+                              [Arg("d" + c, acc, STAR[:1]) for c in CONS], [h, h, h, RK_A[s], dt]))
         if mixed:
             for c in CONS:
                 loops.append(Loop("hilo_add", lo, hi, [Arg(c, RW), Arg("lo_" + c, RW), Arg("d" + c, READ)],
@@ -125,12 +142,13 @@ def chain_loops(n: int, steps: int = 1, mixed: bool = False, re: float = RE) -> 
     return loops
 
 
-def run(ex, n: int, chains: int, steps_per_chain: int = 1, mixed: bool = False, U0: np.ndarray = None):
+def run(ex, n: int, chains: int, steps_per_chain: int = 1, mixed: bool = False, U0: np.ndarray = None,
+        fused: bool = False):
     """Drive `chains` chains of `steps_per_chain` RK3 steps on an executor `ex`."""
     U0 = initial(n) if U0 is None else U0
-    for d in datasets(n, steps_per_chain, "f32" if mixed else "f64", U0, mixed):
+    for d in datasets(n, steps_per_chain, "f32" if mixed else "f64", U0, mixed, fused):
         ex.decl_dat(d)
-    loops = chain_loops(n, steps_per_chain, mixed)
+    loops = chain_loops(n, steps_per_chain, mixed, fused=fused)
     for _ in range(chains):
         for lp in loops:
             ex.enqueue(lp)
