@@ -120,10 +120,13 @@ struct Ctx {
     std::unordered_map<uint64_t, std::vector<std::vector<LaunchDesc>>> descs;  // plan sig -> tiles
     std::unordered_map<uint64_t, GraphSet> graphs;
     std::unordered_map<uint64_t, ChainGraph> chain_graphs;
-    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr, ev_par = nullptr;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
     int force_h = 0, force_depth = 0;
     std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
+    // 1 where the tile's upload / download issued at least one copy and its event was
+    // recorded; an empty phase records nothing and nothing waits for it
+    std::vector<char> up_rec, dn_rec;
     cudaEvent_t ev_pf = nullptr, ev_end = nullptr;
     double* h_params = nullptr;
     size_t h_params_cap = 0;
@@ -700,7 +703,7 @@ static int issue_prefetch(const Plan& P)
     if (P.T < 2 || P.incore) return OC_OK;
     const int T = P.T;
     OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_comp[T - 1], 0));
-    OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 2], 0));
+    if (g->dn_rec[T - 2]) OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 2], 0));
     bool any = false;
     for (size_t di = 0; di < P.dp.size(); ++di) {
         const DatPlan& dp = P.dp[di];
@@ -738,10 +741,10 @@ static int issue_prefetch(const Plan& P)
         g->pf.rows[di] = rows;
         any = any || !rows.empty();
     }
+    if (!any) return OC_OK;   // nothing fetched: no event for the next chain to wait on
     OC_CUDA(cudaEventRecord(g->ev_pf, g->st[1]));
     g->pf.active = true;
     g->pf.sig = P.sig;
-    (void)any;
     return OC_OK;
 }
 
@@ -938,6 +941,10 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                                 cudaMemcpyHostToDevice, s0));
         OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.paramsf_off, hpf, (size_t)P.nparams * 4,
                                 cudaMemcpyHostToDevice, s0));
+        // the tile uploads share the host-to-device copy engine: queued at the same time,
+        // a bulk upload can go first and hold the first compute back for a whole tile
+        OC_CUDA(cudaEventRecord(g->ev_par, s0));
+        OC_CUDA(cudaStreamWaitEvent(s1, g->ev_par, 0));
     }
 
     const bool use_graphs = !trial && !capturing && (g->flags & OC_FLAG_GRAPHS) != 0;
@@ -1009,6 +1016,8 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
             if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
         }
         const int T = P.T, k = P.depth - 2;
+        g->up_rec.assign(std::max(T, 1), 0);
+        g->dn_rec.assign(std::max(T, 1), 0);
         for (int p = -k; p <= T; ++p) {
             const int u = p + k;
             // Issue order inside a phase: with lookahead (k >= 1) compute and download
@@ -1016,8 +1025,8 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
             // upload calls; with k == 0 the upload of tile p must be issued before the
             // compute that waits for it.
             if (k >= 1 && p >= 0 && p < T) {
-                OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
-                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
+                if (g->up_rec[p]) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
+                if (p - 2 >= 0 && g->dn_rec[p - 2]) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
                 rc = trace_begin(p, 1, s0);
                 if (!rc) rc = run_compute(p);
                 if (!rc) rc = trace_end(s0, 0.0);
@@ -1026,7 +1035,7 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
             }
             if (u >= 0 && u < T) {
                 if (p - 1 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_comp[p - 1], 0));
-                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_down[p - 2], 0));
+                if (p - 2 >= 0 && g->dn_rec[p - 2]) OC_CUDA(cudaStreamWaitEvent(s1, g->ev_down[p - 2], 0));
                 const double up0 = S.h2d_bytes;
                 rc = trace_begin(u, 0, s1);
                 if (rc) return rc;
@@ -1045,11 +1054,14 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                 }
                 rc = trace_end(s1, S.h2d_bytes - up0);
                 if (rc) return rc;
-                OC_CUDA(cudaEventRecord(g->ev_up[u], s1));
+                // (an event recorded behind stream waits alone was seen to release its
+                // waiters only when the stream's next copy completed: skip it)
+                g->up_rec[u] = S.h2d_bytes > up0;
+                if (g->up_rec[u]) OC_CUDA(cudaEventRecord(g->ev_up[u], s1));
             }
             if (k == 0 && p >= 0 && p < T) {
-                OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
-                if (p - 2 >= 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
+                if (g->up_rec[p]) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_up[p], 0));
+                if (p - 2 >= 0 && g->dn_rec[p - 2]) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[p - 2], 0));
                 rc = trace_begin(p, 1, s0);
                 if (!rc) rc = run_compute(p);
                 if (!rc) rc = trace_end(s0, 0.0);
@@ -1074,7 +1086,8 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                 }
                 rc = trace_end(s2, S.d2h_bytes - dn0);
                 if (rc) return rc;
-                OC_CUDA(cudaEventRecord(g->ev_down[q], s2));
+                g->dn_rec[q] = S.d2h_bytes > dn0;
+                if (g->dn_rec[q]) OC_CUDA(cudaEventRecord(g->ev_down[q], s2));
             }
         }
         if (pf_match) S.prefetched_bytes = g->pf.bytes;
@@ -1107,7 +1120,7 @@ static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, boo
     int rc = OC_OK;
     (void)loops;
     if (trial) {
-        if (!P.incore && P.T > 0) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[P.T - 1], 0));
+        if (!P.incore && P.T > 0 && g->dn_rec[P.T - 1]) OC_CUDA(cudaStreamWaitEvent(s0, g->ev_down[P.T - 1], 0));
         OC_CUDA(cudaEventRecord(g->tm1, s0));
         rc = wait_event(g->tm1, g->timeout_s);
         if (rc) return rc;
@@ -1118,7 +1131,7 @@ static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, boo
     }
     rc = wait_stream(s0);
     if (rc) return rc;
-    if (!graphed && !P.incore && P.T > 0) {
+    if (!graphed && !P.incore && P.T > 0 && g->dn_rec[P.T - 1]) {
         rc = wait_event(g->ev_down[P.T - 1], g->timeout_s);
         if (rc) return rc;
     }
@@ -1343,6 +1356,7 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_j1, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_j2, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_par, cudaEventDisableTiming);
     }
     return OC_OK;
 }
@@ -1369,7 +1383,7 @@ int oc_finalize(void)
             host_free(kv.second.hp, true);
             host_free(kv.second.hr, true);
         }
-        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2}) if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par}) if (e) cudaEventDestroy(e);
         if (g->tm0) cudaEventDestroy(g->tm0);
         if (g->tm1) cudaEventDestroy(g->tm1);
         host_free(g->trial_sink, true);
