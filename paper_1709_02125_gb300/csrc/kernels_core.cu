@@ -14,6 +14,8 @@
 // execute the same instructions per point and agree bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/oc.h"
 #include "kcommon.cuh"
 #include "launch.h"
@@ -168,10 +170,32 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_lean(const __grid_constan
     }
 }
 
-// LINCOMB for launches whose rows do not cross a slab end (the common case: a slab
-// wraps once per S rows): a row is one 32-bit multiply-add away from the sample's base.
+// Row of a block-row window in a cyclic slab with 32-bit element offsets. `rel` is the
+// slot of the window's first row; rows r >= S - rel wrap to the slab start. The wrap
+// test is uniform over the block, so only the one window per slab that straddles the
+// slab end takes the per-row select.
+template <typename T, int R>
+__device__ __forceinline__ void ring_rows(const T* base, int sl0, int r0, int S, int re, int nr, T (&val)[R])
+{
+    int rel = sl0 + r0;
+    if (rel >= S) rel -= S;
+    const T* q = base + rel * re;
+    const int w = S - rel;
+    if (w >= R) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) val[r] = (R <= nr || r < nr) ? __ldg(q + r * re) : T(0);
+    } else {
+        const int sre = S * re;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            val[r] = (R <= nr || r < nr) ? __ldg(q + (r * re - (r >= w ? sre : 0))) : T(0);
+    }
+}
+
+// LINCOMB with ring addressing (launch.h: `ring`): the samples and their order are
+// those of k_lincomb; each sample's rows come from ring_rows.
 template <typename T, int R, int M>
-__global__ void __launch_bounds__(kThreadsX) k_lincomb_nowrap(const __grid_constant__ LaunchDesc d)
+__global__ void __launch_bounds__(kThreadsX) k_lincomb_ring(const __grid_constant__ LaunchDesc d)
 {
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
@@ -185,13 +209,10 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_nowrap(const __grid_const
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const SampleRec& sr = d.srec[m];
-        const int re = d.sre[m];
         const T c = cp[1 + m];
         const T* p = reinterpret_cast<const T*>(sr.p0) + yl * sr.pitch + x;
-        const int o = (sr.sl0 + r0) * re;
         T val[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) val[r] = (R <= nr || r < nr) ? __ldg(p + (o + r * re)) : T(0);
+        ring_rows<T, R>(p, sr.sl0, r0, sr.S, d.sre[m], nr, val);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (m == 0) { acc[r] = c * val[r]; x0[r] = val[r]; }
@@ -214,10 +235,15 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_nowrap(const __grid_const
     }
     const SampleRec& od = d.orec;
     T* op = const_cast<T*>(reinterpret_cast<const T*>(od.p0)) + yl * od.pitch + x;
-    const int oo = (od.sl0 + r0) * d.ore;
+    int rel = od.sl0 + r0;
+    if (rel >= od.S) rel -= od.S;
+    const int re = d.ore;
+    T* q = op + rel * re;
+    const int w = od.S - rel;
+    const int sre = od.S * re;
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        if (R <= nr || r < nr) op[oo + r * d.ore] = acc[r];
+        if (R <= nr || r < nr) q[r * re - (r >= w ? sre : 0)] = acc[r];
 }
 
 template <typename T, int R>
@@ -359,6 +385,22 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(const double* __restric
     if (threadIdx.x == 0) *out = acc;
 }
 
+// Halo-strip upload (launch.h StripBatch): block row y = job, threads stride over the
+// job's (line, word) pairs. Host memory is read with cache-volatile loads, so a line
+// the copy engines wrote back to the host since is fetched again.
+constexpr int kStripThreads = 256;
+__global__ void __launch_bounds__(kStripThreads) k_strip_copy(const __grid_constant__ StripBatch b)
+{
+    const StripJob& j = b.job[blockIdx.y];
+    const long long n = (long long)j.lines * j.words;
+    for (long long i = (long long)blockIdx.x * kStripThreads + threadIdx.x; i < n;
+         i += (long long)gridDim.x * kStripThreads) {
+        const long long line = i / j.words;
+        const long long o = line * j.pitch + 4 * (i - line * j.words);
+        *reinterpret_cast<unsigned int*>(j.dst + o) = __ldcv(reinterpret_cast<const unsigned int*>(j.src + o));
+    }
+}
+
 template <typename F>
 cudaError_t launch_pointwise(const LaunchDesc& d, cudaStream_t st, F kern)
 {
@@ -389,7 +431,7 @@ cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
-    if (d.nowrap) return launch_rows(d, st, k_lincomb_nowrap<T, kLeanRows, M>, kLeanRows);
+    if (d.ring) return launch_rows(d, st, k_lincomb_ring<T, kLeanRows, M>, kLeanRows);
     if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
     return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
 }
@@ -434,6 +476,16 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
     default:
         return launch_physics(d, st);
     }
+}
+
+cudaError_t launch_strips(const StripBatch& b, cudaStream_t st)
+{
+    if (b.njobs <= 0) return cudaSuccess;
+    long long most = 1;
+    for (int k = 0; k < b.njobs; ++k) most = std::max(most, (long long)b.job[k].lines * b.job[k].words);
+    const int bx = (int)std::min<long long>(64, (most + kStripThreads - 1) / kStripThreads);
+    k_strip_copy<<<dim3(bx, b.njobs), kStripThreads, 0, st>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_combine(const double* part, long long n, int op, double* out, cudaStream_t st)

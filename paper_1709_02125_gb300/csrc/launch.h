@@ -57,12 +57,31 @@ struct LaunchDesc {
     int chunks;                // partials per slow row
     int red_op;                // OC_SUM / OC_MAX / OC_MIN
     int lean;                  // 1: no argument wraps a fast axis; srec / orec are valid
-    int nowrap;                // 1: no slab wrap inside this launch's rows, 32-bit offsets fit
-    int ore;                   // output row stride in elements (nowrap launches)
-    int sre[kLaunchMaxSamples];// sample row strides in elements (nowrap launches)
+    int ring;                  // 1: every slab's element offsets fit 32 bits (ring kernels)
+    int ore;                   // output row stride in elements (ring launches)
+    int sre[kLaunchMaxSamples];// sample row strides in elements (ring launches)
     SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY
     SampleRec srec[kLaunchMaxSamples];
 };
+
+// Strided host-to-device copies done by SM threads that read the pinned host store
+// through its device mapping (the copy engines move narrow strips -- a few bytes per
+// x-line -- one line at a time). Job j copies `lines` lines of `words` 32-bit words:
+// line i from src + i * pitch to dst + i * pitch.
+struct StripJob {
+    const char* src;
+    char* dst;
+    long long pitch;
+    int lines;
+    int words;
+};
+constexpr int kStripJobs = 96;
+struct StripBatch {
+    int njobs;
+    int pad_;
+    StripJob job[kStripJobs];
+};
+cudaError_t launch_strips(const StripBatch& b, cudaStream_t stream);
 
 // Launch one loop tile on `stream`. Returns cudaSuccess or the launch error.
 cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t stream);

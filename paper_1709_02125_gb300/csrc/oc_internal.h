@@ -32,6 +32,7 @@ struct Dat {
     int nrows = 0;           // slow rows including halos
     int y0 = 0;              // slow index of the first row (= -hlo[slow])
     void* host = nullptr;    // pinned host store, nrows * row_elems * esz bytes
+    char* host_dev = nullptr;  // the store's device mapping (null: not mapped)
     bool host_pinned = false;
     // residency (in-core mode keeps the whole dataset in the arena)
     bool resident = false;

@@ -218,9 +218,22 @@ static void host_free(void* p, bool pinned)
 // Copies between the pinned store and a slab. Rows [a, b) of dataset d go to slots
 // (y - y0) mod S of the slab at `slab`; a range crossing the slab end is split.
 // With x0 < x1 (uploads of rows first written over x in [x0, x1)) only the x columns
-// outside [x0, x1) are copied: two strided copies over every x-line of the rows.
+// outside [x0, x1) are copied: two strided copies over every x-line of the rows, added
+// to `strips` (an SM-driven copy launched by the caller) when the host store is mapped,
+// else issued to the copy engines.
+static int flush_strips(StripBatch& sb, cudaStream_t s, oc_stats_t* S)
+{
+    if (sb.njobs == 0) return OC_OK;
+    cudaError_t e = launch_strips(sb, s);
+    if (e != cudaSuccess) return fail(OC_ERR_CUDA, "strip upload launch failed: %s", cudaGetErrorString(e));
+    if (S) S->kernel_launches++;
+    sb.njobs = 0;
+    return OC_OK;
+}
+
 static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cudaStream_t s,
-                     double& bytes, int x0 = 0, int x1 = 0, char* host_override = nullptr)
+                     double& bytes, int x0 = 0, int x1 = 0, char* host_override = nullptr,
+                     StripBatch* strips = nullptr, oc_stats_t* stats = nullptr)
 {
     const long long rb = d.row_bytes();
     const size_t lp = (size_t)d.pitch * d.esz;
@@ -239,9 +252,23 @@ static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cud
             char* dsts[2] = {up ? dev + c0 * d.esz : host + c0 * d.esz, up ? dev + c1 * d.esz : host + c1 * d.esz};
             const char* srcs[2] = {up ? host + c0 * d.esz : dev + c0 * d.esz, up ? host + c1 * d.esz : dev + c1 * d.esz};
             const long long w[2] = {cl, cr};
+            const bool sm_copy = up && strips && d.host_dev && !host_override;
             for (int k = 0; k < 2; ++k)
                 if (w[k] > 0) {
-                    OC_CUDA(cudaMemcpy2DAsync(dsts[k], lp, srcs[k], lp, (size_t)w[k] * d.esz, lines, kind, s));
+                    if (sm_copy) {
+                        if (strips->njobs == kStripJobs) {
+                            int r = flush_strips(*strips, s, stats);
+                            if (r) return r;
+                        }
+                        StripJob& j = strips->job[strips->njobs++];
+                        j.src = d.host_dev + (srcs[k] - (const char*)d.host);
+                        j.dst = dsts[k];
+                        j.pitch = (long long)lp;
+                        j.lines = (int)lines;
+                        j.words = (int)(w[k] * d.esz / 4);
+                    } else {
+                        OC_CUDA(cudaMemcpy2DAsync(dsts[k], lp, srcs[k], lp, (size_t)w[k] * d.esz, lines, kind, s));
+                    }
                     bytes += (double)w[k] * d.esz * lines;
                 }
         } else {
@@ -369,16 +396,13 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                     for (int m = 0; m < ns; ++m)
                         d.srec[m] = rec(d.v[d.sarg[m]], d.soff[m][0], lp.ndim == 3 ? d.soff[m][1] : 0, d.soff[m][sa]);
                     d.lean = 1;
-                    // no slab wrap across this launch's rows and 32-bit element offsets:
-                    // the kernels then address a row with one multiply-add
-                    const long long rows = e - s;
-                    auto fits = [&](const SampleRec& r) {
-                        return r.sl0 + rows <= r.S && (long long)r.S * r.row_elems < (1LL << 31);
-                    };
-                    bool nw = fits(d.orec);
-                    for (int m = 0; m < ns && nw; ++m) nw = fits(d.srec[m]);
-                    if (nw) {
-                        d.nowrap = 1;
+                    // 32-bit element offsets over every slab: the ring kernels address a
+                    // row with one multiply-add (and a select only where a slab wraps)
+                    auto fits = [&](const SampleRec& r) { return (long long)r.S * r.row_elems < (1LL << 31); };
+                    bool ok = fits(d.orec);
+                    for (int m = 0; m < ns && ok; ++m) ok = fits(d.srec[m]);
+                    if (ok) {
+                        d.ring = 1;
                         d.ore = (int)d.orec.row_elems;
                         for (int m = 0; m < ns; ++m) d.sre[m] = (int)d.srec[m].row_elems;
                     }
@@ -702,6 +726,8 @@ static int issue_prefetch(const Plan& P)
     g->pf.bytes = 0;
     if (P.T < 2 || P.incore) return OC_OK;
     const int T = P.T;
+    StripBatch strips;
+    strips.njobs = 0;
     OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_comp[T - 1], 0));
     if (g->dn_rec[T - 2]) OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 2], 0));
     bool any = false;
@@ -734,13 +760,16 @@ static int issue_prefetch(const Plan& P)
         if (!ok) continue;
         for (const Interval& iv : rows) {
             double b = 0;
-            int r = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, true, g->st[1], b, iv.x0, iv.x1);
+            int r = copy_rows(d, g->arena + dp.off, dp.S, iv.a, iv.b, true, g->st[1], b, iv.x0, iv.x1, nullptr,
+                              &strips, &g->stats);
             if (r) return r;
             g->pf.bytes += b;
         }
         g->pf.rows[di] = rows;
         any = any || !rows.empty();
     }
+    int rs = flush_strips(strips, g->st[1], &g->stats);
+    if (rs) return rs;
     if (!any) return OC_OK;   // nothing fetched: no event for the next chain to wait on
     OC_CUDA(cudaEventRecord(g->ev_pf, g->st[1]));
     g->pf.active = true;
@@ -1039,6 +1068,8 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                 const double up0 = S.h2d_bytes;
                 rc = trace_begin(u, 0, s1);
                 if (rc) return rc;
+                StripBatch strips;
+                strips.njobs = 0;
                 for (size_t di = 0; di < P.dp.size(); ++di) {
                     const DatPlan& dp = P.dp[di];
                     const Dat& d = g->dats[dp.dat];
@@ -1047,11 +1078,14 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                     for (const Interval& iv : dp.up) {
                         if (iv.t != u) continue;
                         rc = for_missing(iv, have, [&](int a, int b) {
-                            return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes, iv.x0, iv.x1);
+                            return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes, iv.x0, iv.x1, nullptr,
+                                             &strips, &S);
                         });
                         if (rc) return rc;
                     }
                 }
+                rc = flush_strips(strips, s1, &S);
+                if (rc) return rc;
                 rc = trace_end(s1, S.h2d_bytes - up0);
                 if (rc) return rc;
                 // (an event recorded behind stream waits alone was seen to release its
@@ -1427,6 +1461,9 @@ int oc_decl_dat(int ndim, const int size[3], const int halo_lo[3], const int hal
         d.host = host_alloc((size_t)d.bytes(), true);
         if (!d.host) return fail(OC_ERR_NOMEM, "oc_decl_dat: pinned allocation of %lld bytes failed", d.bytes());
         d.host_pinned = true;
+        void* mapped = nullptr;
+        if (cudaHostGetDevicePointer(&mapped, d.host, 0) == cudaSuccess) d.host_dev = (char*)mapped;
+        else cudaGetLastError();
         memset(d.host, 0, (size_t)d.bytes());
         if (host_init) {
             const long long ext0 = d.ext(0);
