@@ -121,11 +121,26 @@ def link_bandwidth(torch, nbytes=1 << 30):
             dt = time.perf_counter() - t0
             best = max(best, (2 if name == "duplex" else 1) * nbytes / dt / 1e9)
         out[f"{name}_gbs"] = round(best, 1)
+    # both directions at once in 8 MiB copies issued alternately (the pipeline's copy
+    # size): the rate the tile streams can reach together
+    ch = 8 << 20
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for o in range(0, nbytes, ch):
+            with torch.cuda.stream(s1):
+                d[o:o + ch].copy_(h[o:o + ch], non_blocking=True)
+            with torch.cuda.stream(s2):
+                h2[o:o + ch].copy_(d2[o:o + ch], non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, 2 * nbytes / (time.perf_counter() - t0) / 1e9)
+    out["duplex_8mib_gbs"] = round(best, 1)
     del h, h2, d, d2
     return out
 
 
-def build_workload(name: str, mixed: bool, n: int):
+def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
     """(datasets, reductions, make_step, footprint bytes, cells x timesteps per step).
     make_step(ex) returns a function running one step (one chain) on executor ex."""
     if name == "random":
@@ -170,7 +185,6 @@ def build_workload(name: str, mixed: bool, n: int):
         return dats, reds, make_step, fp, n * n
     if name == "tgv":
         from workloads import tgv
-        spc = 1
         dats = tgv.datasets(n, spc, "f32" if mixed else "f64", tgv.initial(n), mixed)
         loops = tgv.chain_loops(n, spc, mixed)
 
@@ -187,9 +201,10 @@ def build_workload(name: str, mixed: bool, n: int):
 
 
 def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps, warmup, n, dist,
-                profile_kernel=None):
+                profile_kernels=None, spc=1):
     from paper_1709_02125_gb300 import oc
-    dats, reds, make_step, fp, ct = build_workload(workload, mixed, n)
+    dats, reds, make_step, fp, ct = build_workload(workload, mixed, n, spc)
+    n_datasets = len(dats)
     budget = int(fp * budget_frac)
     streams = [torch.cuda.Stream() for _ in range(3)]
     arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
@@ -235,16 +250,19 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
             "depth": s1["depth"], "kernel_launches": launches, "graph_replays": s1["graph_replays"],
             "prefetched_bytes": s1["prefetched_bytes"], "sums": vals,
         }
-        if profile_kernel:
+        res["n_datasets"] = n_datasets
+        if profile_kernels:
             # second timed region, same steps, with every launch bracketed by CUDA events on
-            # the compute stream: the dominant kernel's average launch time (kept out of
-            # the headline region because the events add host work between launches)
+            # the compute stream: per-kernel device time, from which the dominant kernel
+            # and its average launch time are taken (kept out of the headline region
+            # because the events add host work between launches)
             ex.set_flag(oc.OC_FLAG_PROFILE, True)
             ex.kernel_stats_reset()
             for _ in range(min(steps, 10)):
                 step()
             torch.cuda.synchronize()
-            res["kstats"] = ex.kernel_stats(profile_kernel)
+            res["kstats"] = {k: ex.kernel_stats(k) for k in profile_kernels}
+            res["kstats"] = {k: v for k, v in res["kstats"].items() if v["launches"] > 0}
             ex.set_flag(oc.OC_FLAG_PROFILE, False)
         return res
     finally:
@@ -334,14 +352,37 @@ def cpu_baseline(n, budget_s=20.0):
 
 
 WORKLOADS = {
-    "random": (WORKLOAD, "lincomb", "k_lincomb<float>", 4096),
-    "euler": ("2-D compressible Euler (MacCormack + 4th-order dissipation), 34 datasets, periodic square, "
-              "CFL min-reduction ends every chain, device budget 1/3 of the footprint", "euler_corr",
-              "k_euler_corr<float>", 15360),
+    # name: (description, kernels whose device time the profiled pass compares, default n)
+    "random": (WORKLOAD, ("lincomb", "reduce"), 4096),
+    "euler": ("2-D compressible Euler (MacCormack + 4th-order dissipation), {nd} datasets, periodic square, "
+              "CFL min-reduction ends every chain, device budget 1/3 of the footprint",
+              ("euler_prim", "euler_flux", "euler_pred", "euler_corr", "euler_dt", "hilo_add"), 15360),
     "tgv": ("3-D compressible Navier-Stokes Taylor-Green vortex (4th-order central, low-storage RK3), "
-            "42 datasets, one RK3 step per chain, device budget 1/3 of the footprint", "ns_rhs",
-            "k_ns_rhs<float>", 640),
+            "{nd} datasets, {spc} RK3 step(s) per chain, device budget 1/3 of the footprint",
+            ("ns_prim", "ns_grad", "ns_flux", "ns_div", "ns_update", "hilo_add"), 640),
 }
+
+
+def kernel_symbol(name: str, dtype: str) -> str:
+    """Device function behind a kernel id (LINCOMB runs as the ring-addressed kernel)."""
+    t = "float" if dtype == "f32" else "double"
+    return f"k_lincomb_ring<{t}>" if name == "lincomb" else f"k_{name}<{t}>"
+
+
+def recorded_traffic(workload: str, variant: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu capture
+    (profiles/traffic.json), or None when the kernel source changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(f"{workload}/{variant}")
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1709_02125_gb300", "csrc", rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec
 
 
 def main():
@@ -355,8 +396,9 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore,mixed_incore")
+    ap.add_argument("--spc", type=int, default=1, help="tgv: RK3 steps per chain")
     args = ap.parse_args()
-    desc, prof_kernel, prof_name, n_default = WORKLOADS[args.workload]
+    desc, prof_kernels, n_default = WORKLOADS[args.workload]
     args.n = args.n or n_default
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -400,25 +442,32 @@ def main():
         if name == args.variants.split(",")[0]:
             with Clocks(local) as clk:
                 results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
-                                            args.warmup, args.n, dist, profile_kernel=prof_kernel)
+                                            args.warmup, args.n, dist, profile_kernels=prof_kernels, spc=args.spc)
         else:
             results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
-                                        args.warmup, args.n, dist)
+                                        args.warmup, args.n, dist, spc=args.spc)
     head_name = args.variants.split(",")[0]
     head = results[head_name]
     N = world
     value = N * head["cells_per_step"] * args.steps / head["device_s"]
     e2e_value = N * head["cells_per_step"] * args.steps / head["wall_s"]
     hbm_peak, peak_kind = _peaks()
-    ks = head.get("kstats") or {}
+    kall = head.get("kstats") or {}
     roof = None
-    if ks.get("ms"):
+    if kall:
+        top = max(kall, key=lambda k: kall[k]["ms"])
+        ks = kall[top]
+        total_ms = sum(v["ms"] for v in kall.values())
         achieved = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": prof_name if head["dtype"] == "f32" else prof_name.replace("float", "double"),
+        tr = recorded_traffic(args.workload, head_name)
+        roof = {"bound": "hbm", "kernel": kernel_symbol(top, head["dtype"]),
                 "achieved": round(achieved, 1), "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None, "launches": ks["launches"],
-                "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
-                "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"]}
+                "frac": round(achieved / hbm_peak, 4),
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "traffic_source": tr["profile"] if tr else None,
+                "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
+                "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"],
+                "share_of_profiled_kernel_time": round(ks["ms"] / total_ms, 4)}
     # binding roofline of the whole pipeline: HBM bytes at peak, link bytes at the link speed
     t_step = head["device_s"] / args.steps
     t_roof = max(head["hbm_bytes_per_step"] / (hbm_peak * 1e9), head["h2d_bytes_per_step"] / (link["h2d_gbs"] * 1e9),
@@ -445,7 +494,7 @@ def main():
         "ms_per_step": head["device_s"] / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": head["dtype"] + ("+f64-reductions" if head["dtype"] == "f32" else ""),
         "data": "synthetic",
-        "config": {"workload": desc, "n": args.n, "variant": head_name,
+        "config": {"workload": desc.format(nd=head["n_datasets"], spc=args.spc), "n": args.n, "variant": head_name,
                    "budget_bytes": head["budget_bytes"], "footprint_bytes": head["footprint_bytes"],
                    "tiles": head["tiles"], "tile_height": head["tile_height"], "depth": head["depth"],
                    "l2": "working set > 129 MB L2 (inputs streamed from host memory): no flush needed",

@@ -73,13 +73,17 @@ extern "C" {
  * OC_FLAG_PREFETCH Sec. 4.1 speculative prefetch: while the last tile of a chain
  *                  runs, upload the first tile of the next chain assuming it has
  *                  the same plan; the next chain uploads only what is missing.
- * OC_FLAG_GRAPHS   capture the kernels of each tile once as a CUDA graph and replay
- *                  it when the same chain shape runs again.
+ * OC_FLAG_GRAPHS   capture a chain once as a CUDA graph and replay it when the same
+ *                  chain shape runs again: the whole chain (copies on all three
+ *                  streams, kernels, reductions, prefetch) when neither TRACE nor
+ *                  PROFILE is set and no in-core upload is pending, else the kernels
+ *                  of each tile.
  * OC_FLAG_DRYRUN   no device at all: chains are analysed and planned (the plan can
  *                  be inspected with oc_plan_*), nothing is executed, and
  *                  oc_reduce / oc_fetch_dat return OC_ERR_STATE. Host-only use.
- * OC_FLAG_PROFILE  bracket every kernel launch with CUDA events on the compute
- *                  stream and accumulate per-kernel device time (oc_kernel_stats).
+ * OC_FLAG_PROFILE  bracket every run of consecutive launches of one kernel id with
+ *                  a pair of CUDA events on the compute stream and accumulate
+ *                  per-kernel device time (oc_kernel_stats).
  * OC_FLAG_TRACE    record the device time line of every tile's upload, compute and
  *                  download of the last flush (oc_trace). */
 #define OC_FLAG_CYCLIC   0x1u
@@ -229,9 +233,11 @@ int oc_set_tiling(int tile_height, int depth);
 /* Copy the counters into *out. */
 int oc_stats(oc_stats_t* out);
 
-/* Per-kernel device time measured with OC_FLAG_PROFILE (accumulated until reset).
- * bytes = algorithmic bytes of the launches (Sec. 5.1 formula: every dataset argument
- * moves its range once, twice if read-write), points = range points. */
+/* Per-kernel device time measured with OC_FLAG_PROFILE (accumulated until reset):
+ * ms = event time of the kernel's launch runs (the gaps between launches of one run
+ * included), launches = their count, bytes = algorithmic bytes of the launches (Sec. 5.1
+ * formula: every dataset argument moves its range once, twice if read-write),
+ * points = range points. */
 typedef struct oc_kernel_stats_t {
     long long launches;
     double ms;

@@ -62,6 +62,7 @@ static int fail(int code, const char* fmt, ...)
 // One profiled launch: events bracketing it on the compute stream.
 struct ProfRec {
     int kernel;
+    int launches;         // consecutive launches of `kernel` between the two events
     double bytes, points;
     cudaEvent_t a, b;
 };
@@ -446,25 +447,40 @@ static int pool_event(cudaEvent_t& ev, bool persistent)
 static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
                             std::vector<ProfRec>* recs = nullptr, bool persistent = false)
 {
+    // With OC_FLAG_PROFILE, each run of consecutive launches of one kernel id is
+    // bracketed by one pair of events (an event between every two launches would
+    // stall the launch pipeline and add its own gap to every launch).
     const bool prof = (g->flags & OC_FLAG_PROFILE) != 0 && !g->trial;
-    for (const LaunchDesc& d : ds) {
+    const unsigned ext = persistent ? cudaEventRecordExternal : cudaEventRecordDefault;
+    for (size_t k = 0; k < ds.size();) {
+        size_t k1 = k + 1;
+        if (prof)
+            while (k1 < ds.size() && ds[k1].kernel == ds[k].kernel) ++k1;
         ProfRec pr{};
         if (prof) {
             int r = pool_event(pr.a, persistent);
             if (!r) r = pool_event(pr.b, persistent);
             if (r) return r;
-            pr.kernel = d.kernel;
-            pr.bytes = launch_bytes(d, pr.points);
+            pr.kernel = ds[k].kernel;
+            pr.launches = (int)(k1 - k);
+            for (size_t j = k; j < k1; ++j) {
+                double pts = 0;
+                pr.bytes += launch_bytes(ds[j], pts);
+                pr.points += pts;
+            }
             // inside a stream capture only an "external" record becomes a graph node
-            OC_CUDA(cudaEventRecordWithFlags(pr.a, s, persistent ? cudaEventRecordExternal : cudaEventRecordDefault));
+            OC_CUDA(cudaEventRecordWithFlags(pr.a, s, ext));
         }
-        cudaError_t e = launch_loop(d, s);
-        if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", d.kernel, cudaGetErrorString(e));
+        for (size_t j = k; j < k1; ++j) {
+            cudaError_t e = launch_loop(ds[j], s);
+            if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", ds[j].kernel, cudaGetErrorString(e));
+        }
         if (prof) {
-            OC_CUDA(cudaEventRecordWithFlags(pr.b, s, persistent ? cudaEventRecordExternal : cudaEventRecordDefault));
+            OC_CUDA(cudaEventRecordWithFlags(pr.b, s, ext));
             if (recs) recs->push_back(pr);
             else g->prof_pending.push_back(pr);
         }
+        k = k1;
     }
     return OC_OK;
 }
@@ -520,7 +536,7 @@ static int collect_profile()
         float ms = 0;
         OC_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
         KStat& k = g->kstats[pr.kernel];
-        k.launches++;
+        k.launches += pr.launches;
         k.ms += ms;
         k.bytes += pr.bytes;
         k.points += pr.points;
