@@ -371,7 +371,8 @@ def kernel_symbol(name: str, dtype: str) -> str:
 
 def recorded_traffic(workload: str, variant: str):
     """DRAM bytes per launch of the dominant kernel from a committed ncu capture
-    (profiles/traffic.json), or None when the kernel source changed since."""
+    (profiles/traffic.json), or None when the kernel's source text (between the
+    recorded markers) changed since."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -379,8 +380,9 @@ def recorded_traffic(workload: str, variant: str):
     rec = json.load(open(p)).get(f"{workload}/{variant}")
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1709_02125_gb300", "csrc", rec["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+    text = open(os.path.join(ROOT, "paper_1709_02125_gb300", "csrc", rec["source"])).read()
+    a, b = text.find(rec["from"]), text.find(rec["to"])
+    if a < 0 or b < a or hashlib.sha256(text[a:b].encode()).hexdigest() != rec["source_sha256"]:
         return None
     return rec
 

@@ -431,8 +431,10 @@ cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
-    if (d.ring) return launch_rows(d, st, k_lincomb_ring<T, kLeanRows, M>, kLeanRows);
-    if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
+    if constexpr (M > 0) {
+        if (d.ring) return launch_rows(d, st, k_lincomb_ring<T, kLeanRows, M>, kLeanRows);
+        if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
+    }
     return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
 }
 

@@ -208,3 +208,32 @@ def test_full_size_random_chain_at_one_third_budget(oracle_lib):
     for c in range(2):
         for k, v in rr[c].items():
             assert abs(rg[c][k] - v) <= 1e-12 * bounds[k]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_lincomb_many_samples(oracle_lib, dtype):
+    """LINCOMB with more samples than the unrolled kernels take (25 and 64 samples run
+    through the generic kernel), tiled and untiled."""
+    n = 96
+    rng = np.random.default_rng(21)
+    F = 6
+    dats = [DatSpec(f"m{f}", (n, n), (2, 2), (2, 2), init=rng.uniform(-1, 1, size=(n + 4, n + 4))) for f in range(F)]
+    offs25 = [(dx, dy) for dy in range(-2, 3) for dx in range(-2, 3)]
+    c = rng.uniform(-1, 1, size=64)
+    loops = [Loop("lincomb", (0, 0), (n, n), [Arg("m0", WRITE), Arg("m1", READ, offs25)],
+                  [0.5] + list(c[:25] * 0.5 / np.abs(c[:25]).sum())),
+             Loop("lincomb", (0, 0), (n, n), [Arg("m2", WRITE)] + [Arg(f"m{f}", READ, offs25[:16]) for f in (0, 1, 3, 4)],
+                  [0.5] + list(c * 0.5 / np.abs(c).sum()))]
+    reds = []
+    if dtype == "f32":
+        dats = [DatSpec(d.name, d.size, d.halo_lo, d.halo_hi, "f32", init=d.init.astype(np.float32)) for d in dats]
+    fp = F * (n + 4) * (n + 4) * (8 if dtype == "f64" else 4)
+    inc, _, st_i = run_gpu(dats, reds, loops, 4 * fp)
+    til, _, st_t = run_gpu(dats, reds, loops, 16 * fp, h=9, depth=3)
+    assert st_i["tiles"] == 1 and st_t["tiles"] > 1
+    for d in dats:
+        assert np.array_equal(inc[d.name], til[d.name]), d.name
+    if dtype == "f64":
+        ref, _ = run_oracle(oracle_lib, dats, reds, loops)
+        for d in dats:
+            assert rel_max(til[d.name], ref[d.name]) <= 1e-12, d.name
