@@ -160,6 +160,29 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
                 return [ex.reduce(r.name) for r in reds]
             return step
         return dats, reds, make_step, fp, 0
+    if name == "euler" and spc > 1:
+        # fixed-dt mode: `spc` steps per chain and no reduction in the chain; dt is half
+        # the CFL step of the initial state, computed once before the timed steps
+        from workloads import euler
+        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed, steps=spc)
+        from workloads.spec import RedSpec
+        reds = [RedSpec("dtmin", "min")]
+
+        def make_step(ex):
+            state = {"src": "A", "dt": None}
+
+            def step():
+                if state["dt"] is None:
+                    ex.enqueue(euler.dt_loop(n, mixed))
+                    state["dt"] = 0.5 * euler.CFL * ex.reduce("dtmin")
+                loops, state["src"] = euler.fixed_dt_chain(n, state["dt"], spc, mixed, state["src"])
+                for lp in loops:
+                    ex.enqueue(lp)
+                ex.flush()
+                return []
+            return step
+        fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)
+        return dats, reds, make_step, fp, n * n * spc
     if name == "euler":
         from workloads import euler
         dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed)
@@ -355,7 +378,8 @@ WORKLOADS = {
     # name: (description, kernels whose device time the profiled pass compares, default n)
     "random": (WORKLOAD, ("lincomb", "reduce"), 4096),
     "euler": ("2-D compressible Euler (MacCormack + 4th-order dissipation), {nd} datasets, periodic square, "
-              "CFL min-reduction ends every chain, device budget 1/3 of the footprint",
+              "{spc} step(s) per chain (1: the CFL min-reduction ends every chain; more: fixed dt, no "
+              "reduction), device budget 1/3 of the footprint",
               ("euler_prim", "euler_flux", "euler_pred", "euler_corr", "euler_dt", "hilo_add"), 15360),
     "tgv": ("3-D compressible Navier-Stokes Taylor-Green vortex (4th-order central, low-storage RK3), "
             "{nd} datasets, {spc} RK3 step(s) per chain, device budget 1/3 of the footprint",
@@ -398,7 +422,7 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore,mixed_incore")
-    ap.add_argument("--spc", type=int, default=1, help="tgv: RK3 steps per chain")
+    ap.add_argument("--spc", type=int, default=1, help="tgv / euler: time steps per chain")
     args = ap.parse_args()
     desc, prof_kernels, n_default = WORKLOADS[args.workload]
     args.n = args.n or n_default

@@ -95,6 +95,54 @@ def test_euler_mixed_error_and_totals(oracle_lib):
     assert np.allclose(dtm, dto, rtol=1e-5, atol=0)
 
 
+def euler_fixed_gpu(n, spc, chains, dt, budget, mixed=False, h=0, flags=0):
+    """`chains` chains of `spc` fixed-dt steps each (no reduction in the chain)."""
+    from paper_1709_02125_gb300 import oc
+    G = 2 * spc
+    with oc.Executor(budget, flags=flags) as ex:
+        ex.set_tiling(h, 3 if h else 0)
+        for d in euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed, steps=spc):
+            ex.decl_dat(d)
+        src = "A"
+        for _ in range(chains):
+            loops, src = euler.fixed_dt_chain(n, dt, spc, mixed, src)
+            for lp in loops:
+                ex.enqueue(lp)
+            ex.flush()
+        st = ex.stats()
+        U = np.stack([ex.fetch(f"{src}_{k}")[G:n + G].astype(np.float64) for k in EU])
+        if mixed:
+            U = U + np.stack([ex.fetch(f"L_{k}")[G:n + G].astype(np.float64) for k in EU])
+    return U, st
+
+
+@pytest.mark.parametrize("spc", [2, 3])
+def test_euler_fixed_dt_multistep_chains(oracle_lib, spc):
+    """Several fixed-dt steps per chain (ghost depth 2 per step): untiled == tiled bit for
+    bit, both against the oracle stepping the same dt; mixed within 1e-5."""
+    from oracle import physics
+    n, chains = 96, 2
+    U0 = euler.initial(n)
+    dt = 0.5 * euler.CFL * physics.euler_dt_min(U0, 1.0 / n, 1.0 / n, euler.GAMMA)
+    fp = footprint(euler.datasets(n, steps=spc))
+    Ui, sti = euler_fixed_gpu(n, spc, chains, dt, 4 * fp)
+    Ut, stt = euler_fixed_gpu(n, spc, chains, dt, 4 * fp, h=11)
+    assert sti["tiles"] == 1 and stt["tiles"] > 1
+    assert np.array_equal(Ui, Ut)
+    Uo = U0.copy()
+    for _ in range(spc * chains):
+        physics.euler_step(Uo, dt, 1.0 / n, 1.0 / n, euler.GAMMA, euler.EPS4)
+    for k in range(4):
+        assert rel_max(Ut[k], Uo[k]) <= 1e-12, EU[k]
+    from paper_1709_02125_gb300 import oc
+    fpm = footprint(euler.datasets(n, "f32", None, True, steps=spc))
+    Um, stm = euler_fixed_gpu(n, spc, chains, dt, fpm // 2, mixed=True,
+                              flags=oc.OC_FLAG_CYCLIC | oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS)
+    assert stm["tiles"] > 1
+    for k in range(4):
+        assert rel_l2(Um[k], Uo[k]) <= 1e-5, EU[k]
+
+
 def tgv_gpu(n, chains, spc, budget, mixed=False, h=0, flags=0, fused=False):
     from paper_1709_02125_gb300 import oc
     G = tgv.ghost(spc)

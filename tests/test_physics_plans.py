@@ -35,6 +35,24 @@ def test_euler_chain_plan_is_legal(lib, mixed, h):
     plan_sim.check_legality(plan, loops)
 
 
+@pytest.mark.parametrize("steps,mixed", [(2, False), (3, False), (3, True)])
+def test_euler_fixed_dt_chain_plan_is_legal(lib, steps, mixed):
+    """Multi-step fixed-dt Euler chains: accepted (every range stays inside the ghost
+    rows) and their tiled plans are legal."""
+    n = 40
+    with oc.Executor(1 << 30, dryrun=True, flags=oc.OC_FLAG_CYCLIC) as ex:
+        ex.set_tiling(7, 3)
+        for d in euler.datasets(n, "f32" if mixed else "f64", None, mixed, steps=steps):
+            ex.decl_dat(d)
+        loops, _ = euler.fixed_dt_chain(n, 1e-3, steps, mixed)
+        for lp in loops:
+            ex.enqueue(lp)
+        ex.flush()
+        plan = ex.plan()
+    assert plan["tiles"] > 1
+    plan_sim.check_legality(plan, loops)
+
+
 @pytest.mark.parametrize("steps,mixed", [(1, False), (2, False), (1, True)])
 def test_tgv_chain_plan_is_legal(lib, steps, mixed):
     n = 12

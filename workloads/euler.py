@@ -45,9 +45,14 @@ def initial(n: int, edge: float = 1.5) -> np.ndarray:
     return U
 
 
-def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = False) -> List[DatSpec]:
-    """Datasets of the chain. Conserved sets A and B have halo 2 in y; the rest 1."""
+def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = False,
+             steps: int = 1) -> List[DatSpec]:
+    """Datasets of the chain. Conserved sets have 2 ghost rows per step of the chain in
+    y (one step reads U at y +- 2); the intermediates one row more than the widest range
+    a loop computes them over."""
     per = (0, 1)
+    gc = 2 * steps                 # ghost rows of the conserved variables
+    gi = 2 * (steps - 1) + 1       # ghost rows of the per-step intermediates
     ds = []
     names_c = ["r", "mx", "my", "E"]
 
@@ -55,8 +60,8 @@ def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = Fa
         ds.append(DatSpec(name, (n, n), (0, hlo), (0, hhi), dtype, per, init))
 
     def pad(a):
-        out = np.zeros((n + 4, n))
-        out[2:n + 2] = a
+        out = np.zeros((n + 2 * gc, n))
+        out[gc:n + gc] = a
         return out
 
     for k, c in enumerate(names_c):
@@ -64,46 +69,48 @@ def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = Fa
         if mixed:
             hi = init.astype(np.float32) if init is not None else None
             lo = (init - hi.astype(np.float64)).astype(np.float32) if init is not None else None
-            dat(f"A_{c}", 2, 2, hi)
-            dat(f"L_{c}", 2, 2, lo)
-            dat(f"D_{c}", 0, 0)
+            dat(f"A_{c}", gc, gc, hi)
+            dat(f"L_{c}", gc, gc, lo)
+            dat(f"D_{c}", gc - 2, gc - 2)
         else:
-            dat(f"A_{c}", 2, 2, init)
-            dat(f"B_{c}", 2, 2)
+            dat(f"A_{c}", gc, gc, init)
+            dat(f"B_{c}", gc, gc)
     for c in ("u", "v", "p"):
-        dat(c, 1, 1)
+        dat(c, gi, gi)
     for k in range(4):
-        dat(f"F{k}", 1, 1)
-        dat(f"G{k}", 1, 1)
-        dat(f"S{k}", 1, 0)
-        dat(f"H{k}", 1, 0)
-        dat(f"K{k}", 1, 0)
+        dat(f"F{k}", gi, gi)
+        dat(f"G{k}", gi, gi)
+        dat(f"S{k}", gi, gi - 1)
+        dat(f"H{k}", gi, gi - 1)
+        dat(f"K{k}", gi, gi - 1)
     for c in ("us", "vs", "ps"):
-        dat(c, 1, 0)
+        dat(c, gi, gi - 1)
     return ds
 
 
 def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool = False,
-                red: str = "dtmin") -> List[Loop]:
-    """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L)."""
+                red: str = "dtmin", ext: int = 0, with_dt: bool = True) -> List[Loop]:
+    """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L),
+    computing the new state over rows [-ext, n + ext) (ghost rows a later step of the
+    same chain reads), optionally followed by the CFL min-reduction."""
     lx = ly = dt / (1.0 / n)
     c = ["r", "mx", "my", "E"]
     U = [f"{src}_{k}" for k in c]
     S = [f"S{k}" for k in range(4)]
-    o = [(0, 0)]
+    e = ext
     loops = [
-        Loop("euler_prim", (0, -1), (n, n + 1), [Arg(u, READ) for u in U] +
+        Loop("euler_prim", (0, -e - 1), (n, n + e + 1), [Arg(u, READ) for u in U] +
              [Arg("u", WRITE), Arg("v", WRITE), Arg("p", WRITE)], [GAMMA]),
-        Loop("euler_flux", (0, -1), (n, n + 1), [Arg(u, READ) for u in U] +
+        Loop("euler_flux", (0, -e - 1), (n, n + e + 1), [Arg(u, READ) for u in U] +
              [Arg("u", READ), Arg("v", READ), Arg("p", READ)] +
              [Arg(f"F{k}", WRITE) for k in range(4)] + [Arg(f"G{k}", WRITE) for k in range(4)], []),
-        Loop("euler_pred", (0, -1), (n, n), [Arg(u, READ) for u in U] +
+        Loop("euler_pred", (0, -e - 1), (n, n + e), [Arg(u, READ) for u in U] +
              [Arg(f"F{k}", READ, [(0, 0), (1, 0)]) for k in range(4)] +
              [Arg(f"G{k}", READ, [(0, 0), (0, 1)]) for k in range(4)] +
              [Arg(s, WRITE) for s in S], [lx, ly]),
-        Loop("euler_prim", (0, -1), (n, n), [Arg(s, READ) for s in S] +
+        Loop("euler_prim", (0, -e - 1), (n, n + e), [Arg(s, READ) for s in S] +
              [Arg("us", WRITE), Arg("vs", WRITE), Arg("ps", WRITE)], [GAMMA]),
-        Loop("euler_flux", (0, -1), (n, n), [Arg(s, READ) for s in S] +
+        Loop("euler_flux", (0, -e - 1), (n, n + e), [Arg(s, READ) for s in S] +
              [Arg("us", READ), Arg("vs", READ), Arg("ps", READ)] +
              [Arg(f"H{k}", WRITE) for k in range(4)] + [Arg(f"K{k}", WRITE) for k in range(4)], []),
     ]
@@ -112,19 +119,35 @@ def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool =
                [Arg(f"H{k}", READ, [(0, 0), (-1, 0)]) for k in range(4)] +
                [Arg(f"K{k}", READ, [(0, 0), (0, -1)]) for k in range(4)])
     if not mixed:
-        loops.append(Loop("euler_corr", (0, 0), (n, n), corr_in + [Arg(f"{dst}_{k}", WRITE) for k in c],
+        loops.append(Loop("euler_corr", (0, -e), (n, n + e), corr_in + [Arg(f"{dst}_{k}", WRITE) for k in c],
                           [lx, ly, EPS4, 0.0]))
-        loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"{dst}_{k}", READ) for k in c] + [Arg(red, REDUCE)],
-                          [GAMMA, 1.0 / n, 1.0 / n]))
+        if with_dt:
+            loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"{dst}_{k}", READ) for k in c] + [Arg(red, REDUCE)],
+                              [GAMMA, 1.0 / n, 1.0 / n]))
     else:
-        loops.append(Loop("euler_corr", (0, 0), (n, n), corr_in + [Arg(f"D_{k}", WRITE) for k in c],
+        loops.append(Loop("euler_corr", (0, -e), (n, n + e), corr_in + [Arg(f"D_{k}", WRITE) for k in c],
                           [lx, ly, EPS4, 1.0]))
         for k in c:
-            loops.append(Loop("hilo_add", (0, 0), (n, n), [Arg(f"A_{k}", RW), Arg(f"L_{k}", RW),
-                                                           Arg(f"D_{k}", READ)], [1.0]))
-        loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"A_{k}", READ) for k in c] +
-                          [Arg(f"L_{k}", READ) for k in c] + [Arg(red, REDUCE)], [GAMMA, 1.0 / n, 1.0 / n]))
+            loops.append(Loop("hilo_add", (0, -e), (n, n + e), [Arg(f"A_{k}", RW), Arg(f"L_{k}", RW),
+                                                                Arg(f"D_{k}", READ)], [1.0]))
+        if with_dt:
+            loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"A_{k}", READ) for k in c] +
+                              [Arg(f"L_{k}", READ) for k in c] + [Arg(red, REDUCE)], [GAMMA, 1.0 / n, 1.0 / n]))
     return loops
+
+
+def fixed_dt_chain(n: int, dt: float, steps: int, mixed: bool = False, src: str = "A") -> Tuple[List[Loop], str]:
+    """`steps` MacCormack steps of one fixed dt as one chain with no reduction (the
+    multi-timestep chains of Sec. 5.3); step j computes its new state over the ghost
+    rows the remaining steps read, 2 per step. Datasets: datasets(..., steps=steps).
+    Returns (loops, prefix of the final state)."""
+    loops: List[Loop] = []
+    a, b = src, ("B" if src == "A" else "A")
+    for j in range(steps):
+        loops += chain_loops(n, dt, a, b, mixed, ext=2 * (steps - 1 - j), with_dt=False)
+        if not mixed:
+            a, b = b, a
+    return loops, ("A" if mixed else a)
 
 
 def totals_loops(n: int, names: List[str], reds: List[str], lo_names: List[str] = None) -> List[Loop]:
