@@ -40,16 +40,27 @@ __device__ __forceinline__ const T* elem(const DView& v, int x, int yl, int s)
     return col_ptr<T>(v, x, yl) + (long long)first_slot(v, s) * v.row_elems;
 }
 
+// The same element with 32-bit offset arithmetic, for launches whose views all keep
+// slot * row_elems below 2^31 (LaunchDesc::o32).
 template <typename T>
-__device__ __forceinline__ T ld(const DView& v, int x, int yl, int s)
+__device__ __forceinline__ const T* elem32(const DView& v, int x, int yl, int s)
 {
-    return __ldg(elem<T>(v, x, yl, s));
+    if (v.periodic & 1) x = wrap1(x, v.nx);
+    if (v.periodic & 2) yl = wrap1(yl, v.ny);
+    const int off = first_slot(v, s) * (int)v.row_elems + (yl + v.oy) * (int)v.pitch + v.ox + x;
+    return reinterpret_cast<const T*>(v.base) + off;
 }
 
-template <typename T>
+template <typename T, bool O32 = false>
+__device__ __forceinline__ T ld(const DView& v, int x, int yl, int s)
+{
+    return __ldg(O32 ? elem32<T>(v, x, yl, s) : elem<T>(v, x, yl, s));
+}
+
+template <typename T, bool O32 = false>
 __device__ __forceinline__ void st(const DView& v, int x, int yl, int s, T val)
 {
-    *const_cast<T*>(elem<T>(v, x, yl, s)) = val;
+    *const_cast<T*>(O32 ? elem32<T>(v, x, yl, s) : elem<T>(v, x, yl, s)) = val;
 }
 
 template <typename T>

@@ -46,52 +46,52 @@ __device__ __forceinline__ Pt shift(const LaunchDesc& d, Pt p, int a, int k)
     return p;
 }
 
-template <typename T>
+template <typename T, bool O>
 __device__ __forceinline__ T L(const LaunchDesc& d, int arg, const Pt& p)
 {
-    return ld<T>(d.v[arg], p.x, p.yl, p.s);
+    return ld<T, O>(d.v[arg], p.x, p.yl, p.s);
 }
 
-template <typename T>
+template <typename T, bool O>
 __device__ __forceinline__ void S(const LaunchDesc& d, int arg, const Pt& p, T v)
 {
-    st<T>(d.v[arg], p.x, p.yl, p.s, v);
+    st<T, O>(d.v[arg], p.x, p.yl, p.s, v);
 }
 
 // ------------------------------------------------------------------ Euler -----
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_prim(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
     if (!point_of(d, p)) return;
     const T gamma = params_of<T>(d)[0];
-    const T r = L<T>(d, 0, p), mx = L<T>(d, 1, p), my = L<T>(d, 2, p), E = L<T>(d, 3, p);
+    const T r = L<T, O>(d, 0, p), mx = L<T, O>(d, 1, p), my = L<T, O>(d, 2, p), E = L<T, O>(d, 3, p);
     const T u = mx / r, v = my / r;
     const T pr = (gamma - T(1)) * (E - T(0.5) * (mx * u + my * v));
-    S<T>(d, 4, p, u);
-    S<T>(d, 5, p, v);
-    S<T>(d, 6, p, pr);
+    S<T, O>(d, 4, p, u);
+    S<T, O>(d, 5, p, v);
+    S<T, O>(d, 6, p, pr);
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_flux(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
     if (!point_of(d, p)) return;
-    const T mx = L<T>(d, 1, p), my = L<T>(d, 2, p), E = L<T>(d, 3, p);
-    const T u = L<T>(d, 4, p), v = L<T>(d, 5, p), pr = L<T>(d, 6, p);
+    const T mx = L<T, O>(d, 1, p), my = L<T, O>(d, 2, p), E = L<T, O>(d, 3, p);
+    const T u = L<T, O>(d, 4, p), v = L<T, O>(d, 5, p), pr = L<T, O>(d, 6, p);
     const T ep = E + pr;
-    S<T>(d, 7, p, mx);
-    S<T>(d, 8, p, mx * u + pr);
-    S<T>(d, 9, p, mx * v);
-    S<T>(d, 10, p, ep * u);
-    S<T>(d, 11, p, my);
-    S<T>(d, 12, p, my * u);
-    S<T>(d, 13, p, my * v + pr);
-    S<T>(d, 14, p, ep * v);
+    S<T, O>(d, 7, p, mx);
+    S<T, O>(d, 8, p, mx * u + pr);
+    S<T, O>(d, 9, p, mx * v);
+    S<T, O>(d, 10, p, ep * u);
+    S<T, O>(d, 11, p, my);
+    S<T, O>(d, 12, p, my * u);
+    S<T, O>(d, 13, p, my * v + pr);
+    S<T, O>(d, 14, p, ep * v);
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_pred(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -100,14 +100,14 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_pred(const __grid_constant_
     const Pt px = shift(d, p, 0, 1), py = shift(d, p, 1, 1);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const T U = L<T>(d, k, p);
-        const T F = L<T>(d, 4 + k, p), Fp = L<T>(d, 4 + k, px);
-        const T G = L<T>(d, 8 + k, p), Gp = L<T>(d, 8 + k, py);
-        S<T>(d, 12 + k, p, (U - lx * (Fp - F)) - ly * (Gp - G));
+        const T U = L<T, O>(d, k, p);
+        const T F = L<T, O>(d, 4 + k, p), Fp = L<T, O>(d, 4 + k, px);
+        const T G = L<T, O>(d, 8 + k, p), Gp = L<T, O>(d, 8 + k, py);
+        S<T, O>(d, 12 + k, p, (U - lx * (Fp - F)) - ly * (Gp - G));
     }
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_corr(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -119,21 +119,21 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_corr(const __grid_constant_
     const Pt ym2 = shift(d, p, 1, -2), ym1 = shift(d, p, 1, -1), yp1 = shift(d, p, 1, 1), yp2 = shift(d, p, 1, 2);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const T U = L<T>(d, k, p);
-        const T d4x = (((L<T>(d, k, xm2) - T(4) * L<T>(d, k, xm1)) + T(6) * U) - T(4) * L<T>(d, k, xp1)) +
-                      L<T>(d, k, xp2);
-        const T d4y = (((L<T>(d, k, ym2) - T(4) * L<T>(d, k, ym1)) + T(6) * U) - T(4) * L<T>(d, k, yp1)) +
-                      L<T>(d, k, yp2);
-        const T Us = L<T>(d, 4 + k, p);
-        const T A = lx * (L<T>(d, 8 + k, p) - L<T>(d, 8 + k, xm1));
-        const T B = ly * (L<T>(d, 12 + k, p) - L<T>(d, 12 + k, ym1));
+        const T U = L<T, O>(d, k, p);
+        const T d4x = (((L<T, O>(d, k, xm2) - T(4) * L<T, O>(d, k, xm1)) + T(6) * U) - T(4) * L<T, O>(d, k, xp1)) +
+                      L<T, O>(d, k, xp2);
+        const T d4y = (((L<T, O>(d, k, ym2) - T(4) * L<T, O>(d, k, ym1)) + T(6) * U) - T(4) * L<T, O>(d, k, yp1)) +
+                      L<T, O>(d, k, yp2);
+        const T Us = L<T, O>(d, 4 + k, p);
+        const T A = lx * (L<T, O>(d, 8 + k, p) - L<T, O>(d, 8 + k, xm1));
+        const T B = ly * (L<T, O>(d, 12 + k, p) - L<T, O>(d, 12 + k, ym1));
         const T first = inc ? (Us - U) : (U + Us);
-        S<T>(d, 16 + k, p, T(0.5) * ((first - A) - B) - eps4 * (d4x + d4y));
+        S<T, O>(d, 16 + k, p, T(0.5) * ((first - A) - B) - eps4 * (d4x + d4y));
     }
 }
 
 // CFL candidate of one point; with the low parts present the state is hi + lo.
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kRedThreads) k_euler_dt(const __grid_constant__ LaunchDesc d)
 {
     const T* pm = params_of<T>(d);
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(kRedThreads) k_euler_dt(const __grid_constant_
         T U[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            U[k] = ld<T>(d.v[k], x, yl, s);
-            if (lo) U[k] = U[k] + ld<T>(d.v[4 + k], x, yl, s);
+            U[k] = ld<T, O>(d.v[k], x, yl, s);
+            if (lo) U[k] = U[k] + ld<T, O>(d.v[4 + k], x, yl, s);
         }
         const T r = U[0], u = U[1] / r, v = U[2] / r;
         const T pr = (gamma - T(1)) * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
@@ -155,31 +155,31 @@ __global__ void __launch_bounds__(kRedThreads) k_euler_dt(const __grid_constant_
 }
 
 // --------------------------------------------------------------- Navier-Stokes --
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_prim(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
     if (!point_of(d, p)) return;
     const T gamma = params_of<T>(d)[0], Ma = params_of<T>(d)[1];
-    const T r = L<T>(d, 0, p), ru = L<T>(d, 1, p), rv = L<T>(d, 2, p), rw = L<T>(d, 3, p), rE = L<T>(d, 4, p);
+    const T r = L<T, O>(d, 0, p), ru = L<T, O>(d, 1, p), rv = L<T, O>(d, 2, p), rw = L<T, O>(d, 3, p), rE = L<T, O>(d, 4, p);
     const T u = ru / r, v = rv / r, w = rw / r;
     const T pr = (gamma - T(1)) * (rE - T(0.5) * ((ru * u + rv * v) + rw * w));
-    S<T>(d, 5, p, u);
-    S<T>(d, 6, p, v);
-    S<T>(d, 7, p, w);
-    S<T>(d, 8, p, pr);
-    S<T>(d, 9, p, ((gamma * Ma) * Ma) * pr / r);
+    S<T, O>(d, 5, p, u);
+    S<T, O>(d, 6, p, v);
+    S<T, O>(d, 7, p, w);
+    S<T, O>(d, 8, p, pr);
+    S<T, O>(d, 9, p, ((gamma * Ma) * Ma) * pr / r);
 }
 
-template <typename T>
+template <typename T, bool O>
 __device__ __forceinline__ T d1(const LaunchDesc& d, int arg, const Pt& p, int a, T h12)
 {
-    const T fm2 = L<T>(d, arg, shift(d, p, a, -2)), fm1 = L<T>(d, arg, shift(d, p, a, -1));
-    const T fp1 = L<T>(d, arg, shift(d, p, a, 1)), fp2 = L<T>(d, arg, shift(d, p, a, 2));
+    const T fm2 = L<T, O>(d, arg, shift(d, p, a, -2)), fm1 = L<T, O>(d, arg, shift(d, p, a, -1));
+    const T fp1 = L<T, O>(d, arg, shift(d, p, a, 1)), fp2 = L<T, O>(d, arg, shift(d, p, a, 2));
     return ((fm2 - T(8) * fm1) + (T(8) * fp1 - fp2)) / h12;
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_grad(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -188,34 +188,41 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_grad(const __grid_constant__ L
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) S<T>(d, 4 + 3 * f + a, p, d1<T>(d, f, p, a, T(12) * pm[a]));
+        for (int a = 0; a < 3; ++a) S<T, O>(d, 4 + 3 * f + a, p, d1<T, O>(d, f, p, a, T(12) * pm[a]));
 }
 
-// The five fluxes in direction a at point q (arguments: 0-4 U, 5-8 u v w p,
-// 9-20 gradients d(u,v,w,T)/d(x,y,z) in that order).
-template <typename T>
-__device__ __forceinline__ void ns_fluxes(const LaunchDesc& d, const Pt& q, int a, T mu, T kc, T (&f)[5])
+// The 21 inputs of the fluxes at point q (arguments 0-4 U, 5-8 u v w p, 9-20 the
+// gradients d(u,v,w,T)/d(x,y,z) in that order), loaded once.
+template <typename T, bool O>
+__device__ __forceinline__ void ns_inputs(const LaunchDesc& d, const Pt& q, T (&in)[21])
 {
-    const T vel[3] = {L<T>(d, 5, q), L<T>(d, 6, q), L<T>(d, 7, q)};
-    const T pr = L<T>(d, 8, q);
-    const T div = (L<T>(d, 9, q) + L<T>(d, 13, q)) + L<T>(d, 17, q);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) in[k] = L<T, O>(d, k, q);
+}
+
+// The five fluxes in direction a from the inputs of one point.
+template <typename T>
+__device__ __forceinline__ void ns_fluxes(const T (&in)[21], int a, T mu, T kc, T (&f)[5])
+{
+    const T vel[3] = {in[5], in[6], in[7]};
+    const T pr = in[8];
+    const T div = (in[9] + in[13]) + in[17];
     T tau[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const T s = L<T>(d, 9 + 3 * b + a, q) + L<T>(d, 9 + 3 * a + b, q);
+        const T s = in[9 + 3 * b + a] + in[9 + 3 * a + b];
         tau[b] = mu * (b == a ? s - (T(2) / T(3)) * div : s);
     }
-    f[0] = L<T>(d, 1 + a, q);
+    f[0] = in[1 + a];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const T uu = L<T>(d, 1 + i, q) * vel[a];
+        const T uu = in[1 + i] * vel[a];
         f[1 + i] = (i == a ? uu + pr : uu) - tau[i];
     }
-    f[4] = ((L<T>(d, 4, q) + pr) * vel[a] - ((vel[0] * tau[0] + vel[1] * tau[1]) + vel[2] * tau[2])) -
-           kc * L<T>(d, 18 + a, q);
+    f[4] = ((in[4] + pr) * vel[a] - ((vel[0] * tau[0] + vel[1] * tau[1]) + vel[2] * tau[2])) - kc * in[18 + a];
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_rhs(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -229,24 +236,28 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_rhs(const __grid_constant__ La
 #pragma unroll 1
     for (int a = 0; a < 3; ++a) {
         const T h12 = T(12) * pd[4 + a];
-        T fm2[5], fm1[5], fp1[5], fp2[5];
-        ns_fluxes<T>(d, shift(d, p, a, -2), a, mu, kc, fm2);
-        ns_fluxes<T>(d, shift(d, p, a, -1), a, mu, kc, fm1);
-        ns_fluxes<T>(d, shift(d, p, a, 1), a, mu, kc, fp1);
-        ns_fluxes<T>(d, shift(d, p, a, 2), a, mu, kc, fp2);
+        T fm2[5], fm1[5], fp1[5], fp2[5], in[21];
+        ns_inputs<T, O>(d, shift(d, p, a, -2), in);
+        ns_fluxes<T>(in, a, mu, kc, fm2);
+        ns_inputs<T, O>(d, shift(d, p, a, -1), in);
+        ns_fluxes<T>(in, a, mu, kc, fm1);
+        ns_inputs<T, O>(d, shift(d, p, a, 1), in);
+        ns_fluxes<T>(in, a, mu, kc, fp1);
+        ns_inputs<T, O>(d, shift(d, p, a, 2), in);
+        ns_fluxes<T>(in, a, mu, kc, fp2);
 #pragma unroll
         for (int m = 0; m < 5; ++m) R[m] = R[m] - ((fm2[m] - T(8) * fm1[m]) + (T(8) * fp1[m] - fp2[m])) / h12;
     }
     const bool rw = d.access[21] == OC_RW;
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const T du = rw ? A * L<T>(d, 21 + m, p) + dt * R[m] : dt * R[m];
-        S<T>(d, 21 + m, p, du);
+        const T du = rw ? A * L<T, O>(d, 21 + m, p) + dt * R[m] : dt * R[m];
+        S<T, O>(d, 21 + m, p, du);
     }
 }
 
 // The 15 fluxes of the point (same evaluation as the fused kernel's ns_fluxes).
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_flux(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -255,17 +266,19 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_flux(const __grid_constant__ L
     const T gamma = pd[0], Ma = pd[1], Re = pd[2], Pr = pd[3];
     const T mu = Re > T(0) ? T(1) / Re : T(0);
     const T kc = mu / ((((gamma - T(1)) * Ma) * Ma) * Pr);
-#pragma unroll 1
+    T in[21];
+    ns_inputs<T, O>(d, p, in);
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         T f[5];
-        ns_fluxes<T>(d, p, a, mu, kc, f);
+        ns_fluxes<T>(in, a, mu, kc, f);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) S<T>(d, 21 + 3 * m + a, p, f[m]);
+        for (int m = 0; m < 5; ++m) S<T, O>(d, 21 + 3 * m + a, p, f[m]);
     }
 }
 
 // R_m = - sum_a D_a(F_{m,a}) from stored fluxes, then the low-storage RK register.
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
@@ -279,23 +292,23 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ La
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int arg = 3 * m + a;
-            const T fm2 = L<T>(d, arg, shift(d, p, a, -2)), fm1 = L<T>(d, arg, shift(d, p, a, -1));
-            const T fp1 = L<T>(d, arg, shift(d, p, a, 1)), fp2 = L<T>(d, arg, shift(d, p, a, 2));
+            const T fm2 = L<T, O>(d, arg, shift(d, p, a, -2)), fm1 = L<T, O>(d, arg, shift(d, p, a, -1));
+            const T fp1 = L<T, O>(d, arg, shift(d, p, a, 1)), fp2 = L<T, O>(d, arg, shift(d, p, a, 2));
             r = r - ((fm2 - T(8) * fm1) + (T(8) * fp1 - fp2)) / (T(12) * pd[a]);
         }
-        const T du = rw ? A * L<T>(d, 15 + m, p) + dt * r : dt * r;
-        S<T>(d, 15 + m, p, du);
+        const T du = rw ? A * L<T, O>(d, 15 + m, p) + dt * r : dt * r;
+        S<T, O>(d, 15 + m, p, du);
     }
 }
 
-template <typename T>
+template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_update(const __grid_constant__ LaunchDesc d)
 {
     Pt p;
     if (!point_of(d, p)) return;
     const T B = params_of<T>(d)[0];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) S<T>(d, m, p, L<T>(d, m, p) + B * L<T>(d, 5 + m, p));
+    for (int m = 0; m < 5; ++m) S<T, O>(d, m, p, L<T, O>(d, m, p) + B * L<T, O>(d, 5 + m, p));
 }
 
 template <typename K>
@@ -315,27 +328,36 @@ cudaError_t launch_pt(const LaunchDesc& d, cudaStream_t st, K kern)
 cudaError_t launch_physics(const LaunchDesc& d, cudaStream_t st)
 {
     const bool f = d.dtype == OC_F32;
+    const bool o = d.o32 != 0;
+#define OC_PT(K) (f ? (o ? launch_pt(d, st, K<float, true>) : launch_pt(d, st, K<float, false>)) \
+                    : (o ? launch_pt(d, st, K<double, true>) : launch_pt(d, st, K<double, false>)))
     switch (d.kernel) {
-    case OC_K_EULER_PRIM: return f ? launch_pt(d, st, k_euler_prim<float>) : launch_pt(d, st, k_euler_prim<double>);
-    case OC_K_EULER_FLUX: return f ? launch_pt(d, st, k_euler_flux<float>) : launch_pt(d, st, k_euler_flux<double>);
-    case OC_K_EULER_PRED: return f ? launch_pt(d, st, k_euler_pred<float>) : launch_pt(d, st, k_euler_pred<double>);
-    case OC_K_EULER_CORR: return f ? launch_pt(d, st, k_euler_corr<float>) : launch_pt(d, st, k_euler_corr<double>);
+    case OC_K_EULER_PRIM: return OC_PT(k_euler_prim);
+    case OC_K_EULER_FLUX: return OC_PT(k_euler_flux);
+    case OC_K_EULER_PRED: return OC_PT(k_euler_pred);
+    case OC_K_EULER_CORR: return OC_PT(k_euler_corr);
     case OC_K_EULER_DT: {
         const int sa = d.ndim - 1, ns = d.hi[sa] - d.lo[sa];
         if (ns <= 0) return cudaSuccess;
         dim3 grid(d.chunks, ns, 1);
-        if (f) k_euler_dt<float><<<grid, kRedThreads, 0, st>>>(d);
-        else k_euler_dt<double><<<grid, kRedThreads, 0, st>>>(d);
+        if (f) {
+            if (o) k_euler_dt<float, true><<<grid, kRedThreads, 0, st>>>(d);
+            else k_euler_dt<float, false><<<grid, kRedThreads, 0, st>>>(d);
+        } else {
+            if (o) k_euler_dt<double, true><<<grid, kRedThreads, 0, st>>>(d);
+            else k_euler_dt<double, false><<<grid, kRedThreads, 0, st>>>(d);
+        }
         return cudaGetLastError();
     }
-    case OC_K_NS_PRIM: return f ? launch_pt(d, st, k_ns_prim<float>) : launch_pt(d, st, k_ns_prim<double>);
-    case OC_K_NS_GRAD: return f ? launch_pt(d, st, k_ns_grad<float>) : launch_pt(d, st, k_ns_grad<double>);
-    case OC_K_NS_RHS: return f ? launch_pt(d, st, k_ns_rhs<float>) : launch_pt(d, st, k_ns_rhs<double>);
-    case OC_K_NS_UPDATE: return f ? launch_pt(d, st, k_ns_update<float>) : launch_pt(d, st, k_ns_update<double>);
-    case OC_K_NS_FLUX: return f ? launch_pt(d, st, k_ns_flux<float>) : launch_pt(d, st, k_ns_flux<double>);
-    case OC_K_NS_DIV: return f ? launch_pt(d, st, k_ns_div<float>) : launch_pt(d, st, k_ns_div<double>);
+    case OC_K_NS_PRIM: return OC_PT(k_ns_prim);
+    case OC_K_NS_GRAD: return OC_PT(k_ns_grad);
+    case OC_K_NS_RHS: return OC_PT(k_ns_rhs);
+    case OC_K_NS_UPDATE: return OC_PT(k_ns_update);
+    case OC_K_NS_FLUX: return OC_PT(k_ns_flux);
+    case OC_K_NS_DIV: return OC_PT(k_ns_div);
     default: return cudaErrorInvalidValue;
     }
+#undef OC_PT
 }
 
 }  // namespace oc

@@ -58,6 +58,7 @@ struct LaunchDesc {
     int red_op;                // OC_SUM / OC_MAX / OC_MIN
     int lean;                  // 1: no argument wraps a fast axis; srec / orec are valid
     int ring;                  // 1: every slab's element offsets fit 32 bits (ring kernels)
+    int o32;                   // 1: every view's slot * row_elems fits 32 bits (PDE kernels)
     int ore;                   // output row stride in elements (ring launches)
     int sre[kLaunchMaxSamples];// sample row strides in elements (ring launches)
     SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY

@@ -409,6 +409,10 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                     }
                 }
             }
+            // 32-bit element offsets inside every view (PDE kernels)
+            d.o32 = 1;
+            for (int j = 0; j < d.nargs; ++j)
+                if (lp.args[j].access != OC_REDUCE && (long long)d.v[j].S * d.v[j].row_elems >= (1LL << 31)) d.o32 = 0;
             d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
             d.paramsf = (const float*)(g->arena + sb + P.paramsf_off) + P.loop_param[i];
             d.nparams = (int)lp.params.size();
