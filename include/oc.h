@@ -193,7 +193,8 @@ int oc_finalize(void);
  *  periodic_mask bit a: axis a is periodic. A periodic non-slow axis must have zero
  *  halo (kernels that support it wrap indices); a periodic slow axis has its halo
  *  layers refreshed from the opposite end at the start of every chain ("deep
- *  ghosts"), so loops may iterate into them.  *dat_out receives the handle. */
+ *  ghosts": a halo row y takes interior row y mod n), so loops may iterate into
+ *  them.  *dat_out receives the handle. */
 int oc_decl_dat(int ndim, const int size[3], const int halo_lo[3], const int halo_hi[3],
                 int dtype, const void* host_init, int periodic_mask, int* dat_out);
 

@@ -587,6 +587,9 @@ static void enter_resident_layout()
 }
 
 // Refresh the halo rows of a periodic slow axis from the opposite end (deep ghosts).
+// Deep ghost rows of a periodic slow axis on the host: row y < 0 or y >= n takes the
+// interior row y mod n. The rows are copied on several threads when there are tens of
+// MB of them (3-D datasets), since the chain waits for them.
 static int ghost_fill_host(const Dat& d)
 {
     const int sa = d.slow();
@@ -594,8 +597,28 @@ static int ghost_fill_host(const Dat& d)
     const long long rb = d.row_bytes();
     char* h = (char*)d.host;
     auto row = [&](int y) { return h + (long long)(y - d.y0) * rb; };
-    for (int y = -lo; y < 0; ++y) memcpy(row(y), row(y + n), rb);
-    for (int y = n; y < n + hi; ++y) memcpy(row(y), row(y - n), rb);
+    const int ng = lo + hi;
+    auto fill = [&](int k0, int k1) {
+        for (int k = k0; k < k1; ++k) {
+            const int y = k < lo ? k - lo : n + (k - lo);
+            const int src = ((y % n) + n) % n;
+            memcpy(row(y), row(src), (size_t)rb);
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<long long>(std::min<unsigned>(hw, 8), (long long)ng * rb / (4LL << 20));
+    if (nt <= 1) {
+        fill(0, ng);
+        return OC_OK;
+    }
+    std::vector<std::thread> th;
+    const int per = (ng + nt - 1) / nt;
+    for (int t = 1; t < nt; ++t) {
+        const int k0 = t * per, k1 = std::min(ng, k0 + per);
+        if (k0 < k1) th.emplace_back(fill, k0, k1);
+    }
+    fill(0, std::min(ng, per));
+    for (auto& t : th) t.join();
     return OC_OK;
 }
 
@@ -605,10 +628,20 @@ static int ghost_fill_device(const Dat& d, cudaStream_t s)
     const int n = d.size[sa], lo = d.hlo[sa], hi = d.hhi[sa];
     const long long rb = d.row_bytes();
     char* b = g->arena + d.res_off;
-    if (lo > 0) OC_CUDA(cudaMemcpyAsync(b, b + (long long)n * rb, (size_t)lo * rb, cudaMemcpyDeviceToDevice, s));
-    if (hi > 0) OC_CUDA(cudaMemcpyAsync(b + (long long)(n + lo) * rb, b + (long long)lo * rb, (size_t)hi * rb,
-                                        cudaMemcpyDeviceToDevice, s));
-    return OC_OK;
+    auto row = [&](int y) { return b + (long long)(y + lo) * rb; };
+    // ghost row y takes interior row y mod n: runs of consecutive rows, one copy each
+    auto fill = [&](int y, int end) -> int {
+        while (y < end) {
+            const int src = ((y % n) + n) % n;
+            const int len = std::min(end - y, n - src);
+            OC_CUDA(cudaMemcpyAsync(row(y), row(src), (size_t)len * rb, cudaMemcpyDeviceToDevice, s));
+            y += len;
+        }
+        return OC_OK;
+    };
+    int rc = fill(-lo, 0);
+    if (!rc) rc = fill(n, n + hi);
+    return rc;
 }
 
 static bool reads_ghosts(const Plan& P, int di)

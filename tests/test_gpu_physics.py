@@ -165,9 +165,11 @@ def tgv_oracle(n, steps):
     return U
 
 
-@pytest.mark.parametrize("spc,fused", [(1, False), (2, False), (1, True)])
-def test_tgv_fp64_tiled_untiled_oracle(oracle_lib, spc, fused):
-    n, chains = 24, 2
+@pytest.mark.parametrize("spc,fused,n", [(1, False, 24), (2, False, 24), (1, True, 24), (2, False, 16)])
+def test_tgv_fp64_tiled_untiled_oracle(oracle_lib, spc, fused, n):
+    """(n = 16 with two steps per chain: the 24 ghost rows are deeper than the extent,
+    so a ghost row takes an interior row more than one period away.)"""
+    chains = 2
     fp = footprint(tgv.datasets(n, spc, fused=fused))
     Ui, sti = tgv_gpu(n, chains, spc, 4 * fp, fused=fused)
     Ut, stt = tgv_gpu(n, chains, spc, 4 * fp, h=7, fused=fused)
