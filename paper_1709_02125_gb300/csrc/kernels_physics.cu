@@ -58,6 +58,36 @@ __device__ __forceinline__ void S(const LaunchDesc& d, int arg, const Pt& p, T v
     st<T, O>(d.v[arg], p.x, p.yl, p.s, v);
 }
 
+// Address of argument `arg` at point p (the centre of a stencil).
+template <typename T, bool O>
+__device__ __forceinline__ const T* C(const LaunchDesc& d, int arg, const Pt& p)
+{
+    const DView& v = d.v[arg];
+    return O ? elem32<T>(v, p.x, p.yl, p.s) : elem<T>(v, p.x, p.yl, p.s);
+}
+
+// Neighbour at distance k along axis a of the point whose address is c: an offset
+// from the centre (x: elements, y: x-lines, slow axis: slab slots), the full periodic
+// wrap only where a fast periodic axis crosses its end.
+template <typename T, bool O>
+__device__ __forceinline__ T Lk(const LaunchDesc& d, int arg, const Pt& p, const T* c, int a, int k)
+{
+    const DView& v = d.v[arg];
+    if (a == 0) {
+        if ((v.periodic & 1) && (p.x + k < 0 || p.x + k >= v.nx)) return L<T, O>(d, arg, shift(d, p, 0, k));
+        return __ldg(c + k);
+    }
+    if (a == 1 && d.ndim == 3) {
+        if ((v.periodic & 2) && (p.yl + k < 0 || p.yl + k >= v.ny)) return L<T, O>(d, arg, shift(d, p, 1, k));
+        return __ldg(c + (long long)k * v.pitch);
+    }
+    const int s0 = first_slot(v, p.s);
+    int s1 = s0 + k;
+    if (s1 >= v.S) s1 -= v.S;
+    else if (s1 < 0) s1 += v.S;
+    return __ldg(c + (long long)(s1 - s0) * v.row_elems);
+}
+
 // ------------------------------------------------------------------ Euler -----
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_prim(const __grid_constant__ LaunchDesc d)
@@ -97,12 +127,13 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_pred(const __grid_constant_
     Pt p;
     if (!point_of(d, p)) return;
     const T lx = params_of<T>(d)[0], ly = params_of<T>(d)[1];
-    const Pt px = shift(d, p, 0, 1), py = shift(d, p, 1, 1);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const T U = L<T, O>(d, k, p);
-        const T F = L<T, O>(d, 4 + k, p), Fp = L<T, O>(d, 4 + k, px);
-        const T G = L<T, O>(d, 8 + k, p), Gp = L<T, O>(d, 8 + k, py);
+        const T* cF = C<T, O>(d, 4 + k, p);
+        const T* cG = C<T, O>(d, 8 + k, p);
+        const T F = __ldg(cF), Fp = Lk<T, O>(d, 4 + k, p, cF, 0, 1);
+        const T G = __ldg(cG), Gp = Lk<T, O>(d, 8 + k, p, cG, 1, 1);
         S<T, O>(d, 12 + k, p, (U - lx * (Fp - F)) - ly * (Gp - G));
     }
 }
@@ -115,18 +146,19 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_corr(const __grid_constant_
     const T* pm = params_of<T>(d);
     const T lx = pm[0], ly = pm[1], eps4 = pm[2];
     const bool inc = pm[3] != T(0);
-    const Pt xm2 = shift(d, p, 0, -2), xm1 = shift(d, p, 0, -1), xp1 = shift(d, p, 0, 1), xp2 = shift(d, p, 0, 2);
-    const Pt ym2 = shift(d, p, 1, -2), ym1 = shift(d, p, 1, -1), yp1 = shift(d, p, 1, 1), yp2 = shift(d, p, 1, 2);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const T U = L<T, O>(d, k, p);
-        const T d4x = (((L<T, O>(d, k, xm2) - T(4) * L<T, O>(d, k, xm1)) + T(6) * U) - T(4) * L<T, O>(d, k, xp1)) +
-                      L<T, O>(d, k, xp2);
-        const T d4y = (((L<T, O>(d, k, ym2) - T(4) * L<T, O>(d, k, ym1)) + T(6) * U) - T(4) * L<T, O>(d, k, yp1)) +
-                      L<T, O>(d, k, yp2);
+        const T* cU = C<T, O>(d, k, p);
+        const T U = __ldg(cU);
+        const T d4x = (((Lk<T, O>(d, k, p, cU, 0, -2) - T(4) * Lk<T, O>(d, k, p, cU, 0, -1)) + T(6) * U) -
+                       T(4) * Lk<T, O>(d, k, p, cU, 0, 1)) + Lk<T, O>(d, k, p, cU, 0, 2);
+        const T d4y = (((Lk<T, O>(d, k, p, cU, 1, -2) - T(4) * Lk<T, O>(d, k, p, cU, 1, -1)) + T(6) * U) -
+                       T(4) * Lk<T, O>(d, k, p, cU, 1, 1)) + Lk<T, O>(d, k, p, cU, 1, 2);
         const T Us = L<T, O>(d, 4 + k, p);
-        const T A = lx * (L<T, O>(d, 8 + k, p) - L<T, O>(d, 8 + k, xm1));
-        const T B = ly * (L<T, O>(d, 12 + k, p) - L<T, O>(d, 12 + k, ym1));
+        const T* cH = C<T, O>(d, 8 + k, p);
+        const T* cK = C<T, O>(d, 12 + k, p);
+        const T A = lx * (__ldg(cH) - Lk<T, O>(d, 8 + k, p, cH, 0, -1));
+        const T B = ly * (__ldg(cK) - Lk<T, O>(d, 12 + k, p, cK, 1, -1));
         const T first = inc ? (Us - U) : (U + Us);
         S<T, O>(d, 16 + k, p, T(0.5) * ((first - A) - B) - eps4 * (d4x + d4y));
     }
@@ -172,10 +204,10 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_prim(const __grid_constant__ L
 }
 
 template <typename T, bool O>
-__device__ __forceinline__ T d1(const LaunchDesc& d, int arg, const Pt& p, int a, T h12)
+__device__ __forceinline__ T d1(const LaunchDesc& d, int arg, const Pt& p, const T* c, int a, T h12)
 {
-    const T fm2 = L<T, O>(d, arg, shift(d, p, a, -2)), fm1 = L<T, O>(d, arg, shift(d, p, a, -1));
-    const T fp1 = L<T, O>(d, arg, shift(d, p, a, 1)), fp2 = L<T, O>(d, arg, shift(d, p, a, 2));
+    const T fm2 = Lk<T, O>(d, arg, p, c, a, -2), fm1 = Lk<T, O>(d, arg, p, c, a, -1);
+    const T fp1 = Lk<T, O>(d, arg, p, c, a, 1), fp2 = Lk<T, O>(d, arg, p, c, a, 2);
     return ((fm2 - T(8) * fm1) + (T(8) * fp1 - fp2)) / h12;
 }
 
@@ -186,9 +218,11 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_grad(const __grid_constant__ L
     if (!point_of(d, p)) return;
     const T* pm = params_of<T>(d);
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+    for (int f = 0; f < 4; ++f) {
+        const T* c = C<T, O>(d, f, p);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) S<T, O>(d, 4 + 3 * f + a, p, d1<T, O>(d, f, p, a, T(12) * pm[a]));
+        for (int a = 0; a < 3; ++a) S<T, O>(d, 4 + 3 * f + a, p, d1<T, O>(d, f, p, c, a, T(12) * pm[a]));
+    }
 }
 
 // The 21 inputs of the fluxes at point q (arguments 0-4 U, 5-8 u v w p, 9-20 the
@@ -292,8 +326,9 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ La
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int arg = 3 * m + a;
-            const T fm2 = L<T, O>(d, arg, shift(d, p, a, -2)), fm1 = L<T, O>(d, arg, shift(d, p, a, -1));
-            const T fp1 = L<T, O>(d, arg, shift(d, p, a, 1)), fp2 = L<T, O>(d, arg, shift(d, p, a, 2));
+            const T* c = C<T, O>(d, arg, p);
+            const T fm2 = Lk<T, O>(d, arg, p, c, a, -2), fm1 = Lk<T, O>(d, arg, p, c, a, -1);
+            const T fp1 = Lk<T, O>(d, arg, p, c, a, 1), fp2 = Lk<T, O>(d, arg, p, c, a, 2);
             r = r - ((fm2 - T(8) * fm1) + (T(8) * fp1 - fp2)) / (T(12) * pd[a]);
         }
         const T du = rw ? A * L<T, O>(d, 15 + m, p) + dt * r : dt * r;
