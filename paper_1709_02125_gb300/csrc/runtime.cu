@@ -769,9 +769,11 @@ static int select_plan(const std::vector<Loop>& loops, Plan*& out)
 }
 
 // Prefetch the first tile of a chain assumed to repeat this plan (Sec. 4.1). Only
-// rows whose host copy is final before the last download phase and whose slots are
-// not live in the last two phases are fetched; ghost rows of a periodic slow axis
-// are left out (they are refreshed when the next chain starts).
+// rows whose slots are not live in the last two phases (T - 1 and T) are fetched, so
+// the prefetch starts as soon as phase T - 2 is done -- in phase T - 1, where the
+// upload stream has nothing else to move -- and only rows whose host copy is final by
+// then (not downloaded in phases T - 1 or T); ghost rows of a periodic slow axis are
+// left out (they are refreshed when the next chain starts).
 static int issue_prefetch(const Plan& P)
 {
     g->pf.active = false;
@@ -781,8 +783,8 @@ static int issue_prefetch(const Plan& P)
     const int T = P.T;
     StripBatch strips;
     strips.njobs = 0;
-    OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_comp[T - 1], 0));
-    if (g->dn_rec[T - 2]) OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 2], 0));
+    OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_comp[T - 2], 0));
+    if (T >= 3 && g->dn_rec[T - 3]) OC_CUDA(cudaStreamWaitEvent(g->st[1], g->ev_down[T - 3], 0));
     bool any = false;
     for (size_t di = 0; di < P.dp.size(); ++di) {
         const DatPlan& dp = P.dp[di];
@@ -803,7 +805,7 @@ static int issue_prefetch(const Plan& P)
                 int r = y - dp.y0;
                 bool ghost = (d.periodic & (1 << sa)) && (y < 0 || y >= d.size[sa]);
                 if (ghost) continue;
-                if (busy[r % dp.S] || (dp.dl[r] && dp.last[r] >= T - 1)) { ok = false; break; }
+                if (busy[r % dp.S] || (dp.dl[r] && dp.last[r] >= T - 2)) { ok = false; break; }
                 if (!rows.empty() && rows.back().b == y && rows.back().x0 == iv.x0 && rows.back().x1 == iv.x1)
                     rows.back().b = y + 1;
                 else rows.push_back({0, y, y + 1, iv.x0, iv.x1});
