@@ -121,7 +121,8 @@ struct Ctx {
     std::unordered_map<uint64_t, std::vector<std::vector<LaunchDesc>>> descs;  // plan sig -> tiles
     std::unordered_map<uint64_t, GraphSet> graphs;
     std::unordered_map<uint64_t, ChainGraph> chain_graphs;
-    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr, ev_par = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr, ev_par = nullptr,
+                ev_res = nullptr;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
     int force_h = 0, force_depth = 0;
     std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
@@ -1020,15 +1021,17 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
     cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
     int rc = OC_OK;
     const auto& tdesc = g->descs[P.sig];
+    // The compute stream carries no copy of its own: after a copy, a stream's next wait
+    // was seen to be served behind the copy engine's queue, so that the first tile's
+    // kernels started only once the next bulk upload had finished. The parameters go
+    // first on the upload stream; the results come back on the download stream.
     if (P.nparams > 0) {
         OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.params_off, hp, (size_t)P.nparams * 8,
-                                cudaMemcpyHostToDevice, s0));
+                                cudaMemcpyHostToDevice, s1));
         OC_CUDA(cudaMemcpyAsync(g->arena + sb + P.paramsf_off, hpf, (size_t)P.nparams * 4,
-                                cudaMemcpyHostToDevice, s0));
-        // the tile uploads share the host-to-device copy engine: queued at the same time,
-        // a bulk upload can go first and hold the first compute back for a whole tile
-        OC_CUDA(cudaEventRecord(g->ev_par, s0));
-        OC_CUDA(cudaStreamWaitEvent(s1, g->ev_par, 0));
+                                cudaMemcpyHostToDevice, s1));
+        OC_CUDA(cudaEventRecord(g->ev_par, s1));
+        OC_CUDA(cudaStreamWaitEvent(s0, g->ev_par, 0));
     }
 
     const bool use_graphs = !trial && !capturing && (g->flags & OC_FLAG_GRAPHS) != 0;
@@ -1191,9 +1194,12 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
         if (e != cudaSuccess) return fail(OC_ERR_CUDA, "combine launch failed: %s", cudaGetErrorString(e));
         S.kernel_launches++;
     }
-    if (!P.rp.empty())
+    if (!P.rp.empty()) {
+        OC_CUDA(cudaEventRecord(g->ev_res, s0));
+        OC_CUDA(cudaStreamWaitEvent(s2, g->ev_res, 0));
         OC_CUDA(cudaMemcpyAsync(hr, g->arena + sb + P.results_off, P.rp.size() * 8,
-                                cudaMemcpyDeviceToHost, s0));
+                                cudaMemcpyDeviceToHost, s2));
+    }
     if (!trial && !P.incore && (g->flags & OC_FLAG_PREFETCH)) {
         rc = issue_prefetch(P);
         if (rc) return rc;
@@ -1220,8 +1226,8 @@ static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, boo
     }
     rc = wait_stream(s0);
     if (rc) return rc;
-    if (!graphed && !P.incore && P.T > 0 && g->dn_rec[P.T - 1]) {
-        rc = wait_event(g->ev_down[P.T - 1], g->timeout_s);
+    if (!graphed) {   // downloads and the results copy (a whole-chain graph ends on s0)
+        rc = wait_stream(g->st[2]);
         if (rc) return rc;
     }
     for (size_t r = 0; r < P.rp.size(); ++r) {
@@ -1446,6 +1452,7 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_j1, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_j2, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_par, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_res, cudaEventDisableTiming);
     }
     return OC_OK;
 }
@@ -1472,7 +1479,7 @@ int oc_finalize(void)
             host_free(kv.second.hp, true);
             host_free(kv.second.hr, true);
         }
-        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par}) if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res}) if (e) cudaEventDestroy(e);
         if (g->tm0) cudaEventDestroy(g->tm0);
         if (g->tm1) cudaEventDestroy(g->tm1);
         host_free(g->trial_sink, true);
