@@ -98,7 +98,9 @@ extern "C" {
  * OC_PLAN_AUTOTUNE  time every (tile height, depth) candidate of the grid on the
  *                   first execution of a chain shape and keep the fastest.
  * OC_PLAN_LEARNED   MLP prediction from chain features (oc_planner_load), snapped
- *                   to the grid; falls back to AUTOTUNE when no network is loaded. */
+ *                   to the grid; falls back to AUTOTUNE when no network is loaded or
+ *                   when a standardised feature of the chain lies more than 4 training
+ *                   deviations from the training mean (a chain unlike the training set). */
 #define OC_PLAN_FIXED    0
 #define OC_PLAN_AUTOTUNE 1
 #define OC_PLAN_LEARNED  2

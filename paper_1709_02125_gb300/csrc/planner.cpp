@@ -90,7 +90,12 @@ bool planner_predict(const float feat[8], int& grid_idx, int& depth)
     Learned& L = learned();
     if (!L.loaded) return false;
     float x[8], y[2];
-    for (int k = 0; k < 8; ++k) x[k] = (feat[k] - L.mean[k]) / (L.stdv[k] > 0 ? L.stdv[k] : 1.0f);
+    for (int k = 0; k < 8; ++k) {
+        x[k] = (feat[k] - L.mean[k]) / (L.stdv[k] > 0 ? L.stdv[k] : 1.0f);
+        // a chain unlike those the network was trained on: no prediction (the caller
+        // falls back to the autotuner)
+        if (!(std::fabs(x[k]) <= kPlannerMaxZ)) return false;
+    }
     if (mlp_forward(L.params.data(), x, 1, y) != cudaSuccess) return false;
     grid_idx = 0;
     depth = 3;

@@ -11,6 +11,7 @@ namespace oc {
 
 constexpr int kGridN = 8;
 constexpr float kPlannerMargin = 0.03f;  // log2 time ratio an alternative must win by
+constexpr float kPlannerMaxZ = 4.0f;     // standardised feature beyond which the network abstains
 extern const double kGridFrac[kGridN];   // tile height as a fraction of the largest fitting one
 
 void chain_features(const std::vector<Loop>& loops, const std::vector<Dat>& dats, long long budget, float f[8]);

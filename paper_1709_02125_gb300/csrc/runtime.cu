@@ -645,6 +645,9 @@ static int ghost_fill_device(const Dat& d, cudaStream_t s)
     return rc;
 }
 
+// True if the chain reads a ghost row of the dataset before writing it (the row is
+// uploaded, whole or in columns): only then does the ghost copy have to be refreshed.
+// Ghost rows the chain computes first (temporaries extended into the ghosts) need none.
 static bool reads_ghosts(const Plan& P, int di)
 {
     const DatPlan& dp = P.dp[di];
@@ -652,7 +655,7 @@ static bool reads_ghosts(const Plan& P, int di)
     const int sa = d.slow();
     for (int r = 0; r < dp.nrows; ++r) {
         int y = r + dp.y0;
-        if ((y < 0 || y >= d.size[sa]) && dp.first[r] >= 0) return true;
+        if ((y < 0 || y >= d.size[sa]) && dp.first[r] >= 0 && dp.need_up[r]) return true;
     }
     return false;
 }

@@ -101,7 +101,8 @@ def test_learned_planner_decision(bias, expect):
     dats, reds, loops, fp = _chain()
     p = np.zeros(mlp.NPARAMS, dtype=np.float32)
     p[-2:] = bias
-    oc.planner_load(p, np.zeros(8), np.ones(8))
+    # a wide standardisation keeps every feature of the test chain in distribution
+    oc.planner_load(p, np.zeros(8), np.full(8, 1e6))
     _, _, st_l = run_gpu(dats, reds, loops, fp // 3, planner=oc.OC_PLAN_LEARNED)
     gi, depth = expect
     _, _, st_f = run_gpu(dats, reds, loops, fp // 3, depth=depth)
@@ -129,3 +130,21 @@ def test_learned_planner_regret_on_heldout_chains():
     # the learned planner never picks a candidate outside its three options, so its worst
     # case is bounded by the worse of them
     assert learned.mean() <= 3 * fixed.mean() + 0.05
+
+
+def test_learned_planner_abstains_out_of_distribution():
+    """Features far outside the training distribution (here: a standardisation that puts
+    them at thousands of deviations): no prediction, the chain is autotuned instead."""
+    from oracle import mlp
+    from paper_1709_02125_gb300 import oc
+    dats, reds, loops, fp = _chain()
+    p = np.zeros(mlp.NPARAMS, dtype=np.float32)
+    p[-2:] = (0.5, 0.1)                      # would choose depth 4 if it answered
+    oc.planner_load(p, np.zeros(8), np.full(8, 1e-3))
+    with oc.Executor(fp // 3, planner=oc.OC_PLAN_LEARNED) as ex:
+        oc.run_chain(ex, dats, reds, loops)
+        table = ex.autotune_result()
+        st = ex.stats()
+    assert len(table) >= 12
+    best = table[np.argmin(table[:, 2])]
+    assert st["tile_height"] == int(best[0]) and st["depth"] == int(best[1])
