@@ -376,7 +376,9 @@ int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats
         int mid = lo + (hi - lo) / 2;
         if (fits(mid)) lo = mid; else hi = mid;
     }
-    return lo;
+    // the same number of tiles, evened out: no short last tile (a phase of its own)
+    const int T = (span + lo - 1) / lo;
+    return (span + T - 1) / T;
 }
 
 }  // namespace oc

@@ -118,12 +118,14 @@ def test_budget_fit_is_largest_height(lib):
     dats, reds, loops = random_chain.build(n=64, nfields=8, nloops=12, seed=5, with_init=False)
     fp = random_chain.footprint_bytes(64, 8)
     plan, _, _ = dry(fp // 3, dats, reds, loops)
-    h = plan["tile_height"]
-    assert 1 <= h < 64
+    h, T, span = plan["tile_height"], plan["tiles"], plan["slow_rows"]
+    assert 1 <= h < 64 and T > 1
     plan_sim.check_legality(plan, loops)
-    # one more row per tile no longer fits (the fixed rule picks the largest fitting height)
+    # the fixed rule takes the fewest tiles that fit and evens their heights out: one
+    # tile fewer no longer fits
+    assert h == -(-span // T)
     with pytest.raises(oc.OcError) as e:
-        dry(fp // 3, dats, reds, loops, h=h + 1, depth=3)
+        dry(fp // 3, dats, reds, loops, h=-(-span // (T - 1)), depth=3)
     assert e.value.code == oc.OC_ERR_BUDGET
 
 
