@@ -140,6 +140,23 @@ def link_bandwidth(torch, nbytes=1 << 30):
     return out
 
 
+def max_over_ranks(dist, values, device):
+    """Each value's maximum over the ranks (the job takes as long as its slowest replica);
+    the values themselves without a process group."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_throughput(n_ranks: int, units_per_step: float, steps: int, seconds: float) -> float:
+    """Whole-job rate of N independent replicas: every rank processes the same units per
+    step, and the job's time is the slowest rank's."""
+    return n_ranks * units_per_step * steps / seconds
+
+
 def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
     """(datasets, reductions, make_step, footprint bytes, cells x timesteps per step).
     make_step(ex) returns a function running one step (one chain) on executor ex."""
@@ -257,10 +274,7 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         dev_s = e0.elapsed_time(e1) / 1e3
-        if dist:
-            t = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dev_s, wall = float(t[0]), float(t[1])
+        dev_s, wall = max_over_ranks(dist, [dev_s, wall], "cuda")
         s1 = ex.stats()
         res = {
             "dtype": "f32" if mixed else "f64", "budget_bytes": budget, "footprint_bytes": fp,
@@ -475,8 +489,8 @@ def main():
     head_name = args.variants.split(",")[0]
     head = results[head_name]
     N = world
-    value = N * head["cells_per_step"] * args.steps / head["device_s"]
-    e2e_value = N * head["cells_per_step"] * args.steps / head["wall_s"]
+    value = job_throughput(N, head["cells_per_step"], args.steps, head["device_s"])
+    e2e_value = job_throughput(N, head["cells_per_step"], args.steps, head["wall_s"])
     hbm_peak, peak_kind = _peaks()
     kall = head.get("kstats") or {}
     roof = None
@@ -501,7 +515,7 @@ def main():
                  (head["h2d_bytes_per_step"] + head["d2h_bytes_per_step"]) / (link["duplex_gbs"] * 1e9))
     variants_out = {}
     for k, r in results.items():
-        v = N * r["cells_per_step"] * args.steps / r["device_s"]
+        v = job_throughput(N, r["cells_per_step"], args.steps, r["device_s"])
         variants_out[k] = {"value": v, "dtype": r["dtype"], "ms_per_step": r["device_s"] / args.steps * 1e3,
                            "tiles": r["tiles"], "tile_height": r["tile_height"], "depth": r["depth"],
                            "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
