@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
 def test_replica_timing_is_max_over_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
