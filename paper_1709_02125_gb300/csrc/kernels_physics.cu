@@ -22,8 +22,13 @@ namespace {
 
 using namespace dev;
 
+// A point of the launch. With uniform argument geometry (LaunchDesc::uni) the in-row
+// offset (y line and x) is shared by all arguments and computed once; `xin` / `yin` say
+// that the +-2 neighbours along x / y need no periodic wrap.
 struct Pt {
     int x, yl, s;
+    int inrow;
+    bool fast, xin, yin;
 };
 
 __device__ __forceinline__ bool point_of(const LaunchDesc& d, Pt& p)
@@ -33,37 +38,45 @@ __device__ __forceinline__ bool point_of(const LaunchDesc& d, Pt& p)
     const int sa = d.ndim - 1;
     p.yl = d.ndim == 3 ? d.lo[1] + (int)blockIdx.y : 0;
     p.s = d.lo[sa] + (int)blockIdx.z;
+    const DView& v = d.v[0];
+    p.fast = d.uni != 0;
+    p.inrow = (p.yl + v.oy) * (int)v.pitch + v.ox + p.x;
+    p.xin = !(v.periodic & 1) || (p.x >= 2 && p.x < v.nx - 2);
+    p.yin = !(v.periodic & 2) || (p.yl >= 2 && p.yl < v.ny - 2);
     return true;
 }
 
 // neighbour of p at distance k along axis a (a = 0 x, 1 y, 2 slow axis in 3-D;
-// in 2-D axis 1 is the slow axis)
+// in 2-D axis 1 is the slow axis); its addresses are then computed in full
 __device__ __forceinline__ Pt shift(const LaunchDesc& d, Pt p, int a, int k)
 {
     if (a == 0) p.x += k;
     else if (a == 1 && d.ndim == 3) p.yl += k;
     else p.s += k;
+    p.fast = false;
     return p;
+}
+
+// Address of argument `arg` at point p.
+template <typename T, bool O>
+__device__ __forceinline__ const T* C(const LaunchDesc& d, int arg, const Pt& p)
+{
+    const DView& v = d.v[arg];
+    if (O && p.fast)
+        return reinterpret_cast<const T*>(v.base) + (first_slot(v, p.s) * (int)v.row_elems + p.inrow);
+    return O ? elem32<T>(v, p.x, p.yl, p.s) : elem<T>(v, p.x, p.yl, p.s);
 }
 
 template <typename T, bool O>
 __device__ __forceinline__ T L(const LaunchDesc& d, int arg, const Pt& p)
 {
-    return ld<T, O>(d.v[arg], p.x, p.yl, p.s);
+    return __ldg(C<T, O>(d, arg, p));
 }
 
 template <typename T, bool O>
 __device__ __forceinline__ void S(const LaunchDesc& d, int arg, const Pt& p, T v)
 {
-    st<T, O>(d.v[arg], p.x, p.yl, p.s, v);
-}
-
-// Address of argument `arg` at point p (the centre of a stencil).
-template <typename T, bool O>
-__device__ __forceinline__ const T* C(const LaunchDesc& d, int arg, const Pt& p)
-{
-    const DView& v = d.v[arg];
-    return O ? elem32<T>(v, p.x, p.yl, p.s) : elem<T>(v, p.x, p.yl, p.s);
+    *const_cast<T*>(C<T, O>(d, arg, p)) = v;
 }
 
 // Neighbour at distance k along axis a of the point whose address is c: an offset
@@ -74,17 +87,20 @@ __device__ __forceinline__ T Lk(const LaunchDesc& d, int arg, const Pt& p, const
 {
     const DView& v = d.v[arg];
     if (a == 0) {
-        if ((v.periodic & 1) && (p.x + k < 0 || p.x + k >= v.nx)) return L<T, O>(d, arg, shift(d, p, 0, k));
+        const bool wraps = p.fast ? !p.xin : ((v.periodic & 1) && (p.x + k < 0 || p.x + k >= v.nx));
+        if (wraps) return L<T, O>(d, arg, shift(d, p, 0, k));
         return __ldg(c + k);
     }
     if (a == 1 && d.ndim == 3) {
-        if ((v.periodic & 2) && (p.yl + k < 0 || p.yl + k >= v.ny)) return L<T, O>(d, arg, shift(d, p, 1, k));
-        return __ldg(c + (long long)k * v.pitch);
+        const bool wraps = p.fast ? !p.yin : ((v.periodic & 2) && (p.yl + k < 0 || p.yl + k >= v.ny));
+        if (wraps) return L<T, O>(d, arg, shift(d, p, 1, k));
+        return __ldg(c + k * (int)v.pitch);
     }
     const int s0 = first_slot(v, p.s);
     int s1 = s0 + k;
     if (s1 >= v.S) s1 -= v.S;
     else if (s1 < 0) s1 += v.S;
+    if (O) return __ldg(c + (s1 - s0) * (int)v.row_elems);
     return __ldg(c + (long long)(s1 - s0) * v.row_elems);
 }
 

@@ -59,6 +59,9 @@ struct LaunchDesc {
     int lean;                  // 1: no argument wraps a fast axis; srec / orec are valid
     int ring;                  // 1: every slab's element offsets fit 32 bits (ring kernels)
     int o32;                   // 1: every view's slot * row_elems fits 32 bits (PDE kernels)
+    int uni;                   // 1 (with o32): every dataset argument has the same fast-axis
+                               //    extents, periodicity, pitch and origin (PDE kernels
+                               //    then share one in-row offset per point)
     int ore;                   // output row stride in elements (ring launches)
     int sre[kLaunchMaxSamples];// sample row strides in elements (ring launches)
     SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY

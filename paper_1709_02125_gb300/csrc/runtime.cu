@@ -410,10 +410,22 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                     }
                 }
             }
-            // 32-bit element offsets inside every view (PDE kernels)
+            // 32-bit element offsets inside every view (PDE kernels); uniform geometry:
+            // one in-row offset per point serves every argument
             d.o32 = 1;
-            for (int j = 0; j < d.nargs; ++j)
-                if (lp.args[j].access != OC_REDUCE && (long long)d.v[j].S * d.v[j].row_elems >= (1LL << 31)) d.o32 = 0;
+            d.uni = 1;
+            int j0 = -1;
+            for (int j = 0; j < d.nargs; ++j) {
+                if (lp.args[j].access == OC_REDUCE) continue;
+                const DView& v = d.v[j];
+                if ((long long)v.S * v.row_elems >= (1LL << 31)) d.o32 = 0;
+                if (j0 < 0) { j0 = j; continue; }
+                const DView& w = d.v[j0];
+                if (v.nx != w.nx || v.ny != w.ny || v.periodic != w.periodic || v.pitch != w.pitch ||
+                    v.ox != w.ox || v.oy != w.oy)
+                    d.uni = 0;
+            }
+            if (j0 != 0 || !d.o32) d.uni = 0;
             d.params = (const double*)(g->arena + sb + P.params_off) + P.loop_param[i];
             d.paramsf = (const float*)(g->arena + sb + P.paramsf_off) + P.loop_param[i];
             d.nparams = (int)lp.params.size();
