@@ -111,6 +111,10 @@ struct Ctx {
     bool own_arena = false;
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
     bool own_streams = false;
+    // second compute stream for independent loops of one tile, and its events
+    cudaStream_t s0b = nullptr;
+    cudaEvent_t ev_tf = nullptr, ev_tj = nullptr;
+    std::vector<cudaEvent_t> ev_launch;
     std::vector<Dat> dats;
     std::vector<int> red_ops;
     std::vector<double> red_val;
@@ -459,6 +463,60 @@ static int pool_event(cudaEvent_t& ev, bool persistent)
     return OC_OK;
 }
 
+// Launch the kernels of one tile on two compute streams: a loop that shares no dataset
+// with a conflicting access (write/read, read/write, write/write) with its predecessor
+// goes to the other stream, so that independent loops overlap and fill each other's
+// last wave; every conflict with a loop on the other stream becomes an event wait.
+// Program order is kept for every pair of loops that touch a common dataset, so the
+// results are those of the serial order.
+static int run_tile_two_streams(const std::vector<LaunchDesc>& ds, cudaStream_t s)
+{
+    const size_t n = ds.size();
+    while (g->ev_launch.size() < n) {
+        cudaEvent_t e;
+        OC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->ev_launch.push_back(e);
+    }
+    // read / write sets of every launch, keyed by the dataset's device base address
+    auto conflict = [&](const LaunchDesc& a, const LaunchDesc& b) {
+        for (int i = 0; i < a.nargs; ++i) {
+            if (a.access[i] == OC_REDUCE) continue;
+            const bool aw = a.access[i] != OC_READ;
+            for (int j = 0; j < b.nargs; ++j) {
+                if (b.access[j] == OC_REDUCE || a.v[i].base != b.v[j].base) continue;
+                if (aw || b.access[j] != OC_READ) return true;
+            }
+        }
+        return false;
+    };
+    cudaStream_t st2[2] = {s, g->s0b};
+    OC_CUDA(cudaEventRecord(g->ev_tf, s));
+    OC_CUDA(cudaStreamWaitEvent(g->s0b, g->ev_tf, 0));
+    std::vector<int> on(n, 0);
+    bool used_b = false;
+    for (size_t k = 0; k < n; ++k) {
+        int last[2] = {-1, -1};   // latest conflicting launch on each stream
+        for (size_t i = 0; i < k; ++i)
+            if (conflict(ds[i], ds[k])) last[on[i]] = (int)i;
+        int sk;
+        if (k == 0) sk = 0;
+        else if (last[0] < 0 && last[1] < 0) sk = 1 - on[k - 1];        // independent: alternate
+        else sk = last[0] >= last[1] ? 0 : 1;                             // follow the latest conflict
+        const int other = 1 - sk;
+        if (last[other] >= 0) OC_CUDA(cudaStreamWaitEvent(st2[sk], g->ev_launch[last[other]], 0));
+        on[k] = sk;
+        used_b = used_b || sk == 1;
+        cudaError_t e = launch_loop(ds[k], st2[sk]);
+        if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", ds[k].kernel, cudaGetErrorString(e));
+        OC_CUDA(cudaEventRecord(g->ev_launch[k], st2[sk]));
+    }
+    // join: everything after the tile on stream s sees both streams' work
+    OC_CUDA(cudaEventRecord(g->ev_tj, g->s0b));
+    OC_CUDA(cudaStreamWaitEvent(s, g->ev_tj, 0));
+    (void)used_b;
+    return OC_OK;
+}
+
 // Launch the kernels of one tile; with profiling, bracket each with events. `recs`
 // receives the records (persistent events when the launches are being captured).
 static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
@@ -468,6 +526,7 @@ static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
     // bracketed by one pair of events (an event between every two launches would
     // stall the launch pipeline and add its own gap to every launch).
     const bool prof = (g->flags & OC_FLAG_PROFILE) != 0 && !g->trial;
+    if (!prof && !(g->flags & OC_FLAG_TRACE) && g->s0b && ds.size() > 1) return run_tile_two_streams(ds, s);
     const unsigned ext = persistent ? cudaEventRecordExternal : cudaEventRecordDefault;
     for (size_t k = 0; k < ds.size();) {
         size_t k1 = k + 1;
@@ -1468,6 +1527,9 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_j2, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_par, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_res, cudaEventDisableTiming);
+        cudaStreamCreateWithFlags(&c->s0b, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&c->ev_tf, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_tj, cudaEventDisableTiming);
     }
     return OC_OK;
 }
@@ -1477,6 +1539,7 @@ int oc_finalize(void)
     if (!g) return fail(OC_ERR_STATE, "oc_finalize: no context");
     if (!g->dryrun) {
         for (int k = 0; k < 3; ++k) if (g->st[k]) cudaStreamSynchronize(g->st[k]);
+        if (g->s0b) cudaStreamSynchronize(g->s0b);
         for (auto& kv : g->graphs) {
             for (auto ge : kv.second.tiles) if (ge) cudaGraphExecDestroy(ge);
             for (auto& v : kv.second.prof) for (auto& pr : v) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
@@ -1494,7 +1557,10 @@ int oc_finalize(void)
             host_free(kv.second.hp, true);
             host_free(kv.second.hr, true);
         }
-        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res}) if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res, g->ev_tf, g->ev_tj})
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : g->ev_launch) cudaEventDestroy(e);
+        if (g->s0b) cudaStreamDestroy(g->s0b);
         if (g->tm0) cudaEventDestroy(g->tm0);
         if (g->tm1) cudaEventDestroy(g->tm1);
         host_free(g->trial_sink, true);
