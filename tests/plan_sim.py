@@ -98,8 +98,17 @@ def check_legality(plan, loops):
                     assert np.all(tile_i[ok] <= tj[ok]), f"WAR violated: loop {i} -> {j} on {D}"
 
 
-def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
-    """Replay the plan with tagged cyclic slabs; returns (fields, reductions)."""
+def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int], chains: int = 1,
+             prefetch: bool = False, stats: Dict = None):
+    """Replay the plan with tagged cyclic slabs for `chains` repetitions of the chain;
+    returns (fields, reductions of the last chain).
+
+    With `prefetch`, the speculative prefetch of Sec. 4.1 is replayed as the executor
+    issues it: once phase T - 2 of a chain is done, every dataset whose tile-0 upload rows
+    all sit in slots not used by rows live in phases T - 1 and T, and none of which is
+    downloaded in those phases, has those rows copied from the host into its slab; the
+    next chain skips them. The simulation checks that the prefetched slots stay untouched
+    until the next chain reads them."""
     T, k = plan["tiles"], plan["depth"] - 2
     by_handle = {d["dat"]: d for d in plan["dats"]}
     specs = {d.name: d for d in dats}
@@ -142,7 +151,65 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
                     rows[a.name].update(range(s + min(dys), e + max(dys)))
         return rows
 
+    # phases in which each row of each dataset is live (upload ... download), for the
+    # prefetch rule
+    last_live = {n: {} for n in slabs}
     for p in range(-k, T + 1):
+        for n, rows in phase_rows(p).items():
+            for y in rows:
+                last_live[n][y] = max(last_live[n].get(y, p), p)
+
+    def prefetch_rows():
+        out = {}
+        for n, sl in slabs.items():
+            busy = {slot(sl, y) for y, pe in last_live[n].items() if pe >= T - 1}
+            late_dl = {y for t, a, b, _, _ in sl["plan"]["down"] if t >= T - 2 for y in range(a, b)}
+            ivs = [(a, b, x0, x1) for t, a, b, x0, x1 in sl["plan"]["up"] if t == 0]
+            rows = [(y, x0, x1) for a, b, x0, x1 in ivs for y in range(a, b)]
+            if rows and all(slot(sl, y) not in busy and y not in late_dl for y, _, _ in rows):
+                out[n] = rows
+        return out
+
+    def upload_row(n, sl, y, x0, x1):
+        hx = specs[n].halo_lo[0]
+        row = host[n].a[y - sl["y0"]]
+        if x0 < x1:
+            # first written over [x0, x1): only the other columns travel; the written
+            # part holds garbage until then
+            new = np.full_like(row, np.nan)
+            new[..., :x0 + hx] = row[..., :x0 + hx]
+            new[..., x1 + hx:] = row[..., x1 + hx:]
+            row = new
+        sl["data"][slot(sl, y)] = row
+        sl["tag"][slot(sl, y)] = y
+
+    have = {}   # rows prefetched for the next chain, per dataset
+    for c in range(chains):
+        red_vals = {}
+        have = _run_chain(plan, loops, T, k, slabs, host, specs, red_ops, red_vals, oracle, slot, phase_rows,
+                          upload_row, have, prefetch and c + 1 < chains, prefetch_rows, stats)
+    return host, red_vals
+
+
+def _run_chain(plan, loops, T, k, slabs, host, specs, red_ops, red_vals, oracle, slot, phase_rows,
+               upload_row, have, do_prefetch, prefetch_rows, stats):
+    pf = {}
+    pf_slots = {}
+    for p in range(-k, T + 1):
+        if do_prefetch and p == T - 1:
+            # phase T - 2 is done: the prefetch goes in while phases T - 1 and T run
+            pf = prefetch_rows()
+            for n, rows in pf.items():
+                sl = slabs[n]
+                for y, x0, x1 in rows:
+                    upload_row(n, sl, y, x0, x1)
+                pf_slots[n] = {slot(sl, y) for y, _, _ in rows}
+                if stats is not None:
+                    stats["prefetched_rows"] = stats.get("prefetched_rows", 0) + len(rows)
+        if pf_slots and p >= T - 1:
+            for n, rows in phase_rows(p).items():
+                hit = {slot(slabs[n], y) for y in rows} & pf_slots.get(n, set())
+                assert not hit, f"phase {p}: a live row of {n} uses a prefetched slot"
         # all rows the three concurrent operations of this phase touch hold distinct slots
         for n, rows in phase_rows(p).items():
             sl = slabs[n]
@@ -151,20 +218,15 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
         u = p + k
         if 0 <= u < T:
             for n, sl in slabs.items():
+                skip = {y for y, _, _ in have.get(n, [])} if u == 0 else set()
                 for t, a, b, x0, x1 in sl["plan"]["up"]:
                     if t == u:
-                        hx = specs[n].halo_lo[0]
                         for y in range(a, b):
-                            row = host[n].a[y - sl["y0"]]
-                            if x0 < x1:
-                                # first written over [x0, x1): only the other columns
-                                # travel; the written part holds garbage until then
-                                new = np.full_like(row, np.nan)
-                                new[..., :x0 + hx] = row[..., :x0 + hx]
-                                new[..., x1 + hx:] = row[..., x1 + hx:]
-                                row = new
-                            sl["data"][slot(sl, y)] = row
-                            sl["tag"][slot(sl, y)] = y
+                            if y in skip:
+                                # prefetched by the previous chain: still in its slot
+                                assert sl["tag"][slot(sl, y)] == y, f"prefetched row {y} of {n} was overwritten"
+                                continue
+                            upload_row(n, sl, y, x0, x1)
         if 0 <= p < T:
             for i, lp in enumerate(loops):
                 s, e = plan["ranges"][p, i]
@@ -218,7 +280,7 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int]):
                         for y in range(a, b):
                             assert sl["tag"][slot(sl, y)] == y, f"download of {n} row {y}: slot holds another row"
                             host[n].a[y - sl["y0"]] = sl["data"][slot(sl, y)]
-    return host, red_vals
+    return pf
 
 
 def _read_rows(lp, name, s, e, sa):
