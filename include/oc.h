@@ -177,7 +177,11 @@ typedef struct oc_stats_t {
  *                       NULL with arena_bytes == 0: the library allocates the
  *                       budget itself and frees it in oc_finalize.
  *  streams              three cudaStream_t handles (upload, compute, download) owned
- *                       by the caller, or NULL: the library creates its own.
+ *                       by the caller, or NULL: the library creates its own. The
+ *                       library also creates one more compute stream of its own, on
+ *                       which loops of a tile that are independent of their
+ *                       neighbours run concurrently; every tile's work is joined back
+ *                       into the compute stream before anything else waits on it.
  *  flags                OC_FLAG_* bits.  planner_mode: OC_PLAN_*.
  * Errors: OC_ERR_STATE if a context exists; OC_ERR_ARG on an arena smaller than
  * the budget; OC_ERR_CUDA if the device cannot be used (not with OC_FLAG_DRYRUN). */
