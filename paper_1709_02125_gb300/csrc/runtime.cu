@@ -17,6 +17,11 @@
 //   download(tile p) : waits compute(p).
 // Rows shared by consecutive tiles stay in their slot, which replaces the paper's
 // right-edge to left-edge copy between slots (Algorithm 1, finishing phase).
+// The loops of one tile run on stream 0 and, where independent of their neighbours,
+// on a second compute stream that is joined back before the tile's end event. The
+// compute streams carry kernels only: the parameter block goes up on stream 1 and the
+// reduction results come back on stream 2. A repeated chain is captured once as one
+// CUDA graph over all streams and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
