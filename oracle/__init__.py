@@ -43,10 +43,13 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The loaded oracle library. ORACLE_LIB, when set, names a prebuilt library to load
+    instead of oracle/_build/liboracle.so (the mutation tests point it at a copy of the
+    oracle with one planted mistake, to show that the pins catch it)."""
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+        path = os.environ.get("ORACLE_LIB") or build()
+        L = ctypes.CDLL(path)
         P, I = ctypes.c_void_p, ctypes.c_int
         L.or_copy.argtypes = [P, P, P, P, P, P, P]
         L.or_lincomb.argtypes = [P, P, P, P, I, P, P, P, P, P, ctypes.c_double]

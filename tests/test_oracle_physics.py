@@ -81,6 +81,7 @@ def test_euler_entropy_wave_closed_form(phys, axis, k):
     MacCormack factor (with the fourth-order dissipation)."""
     n, eps, a, p0, steps = 32, 1e-2, 0.6, 1.0, 15
     h = 1.0 / n
+    ho = 1.37 * h      # spacing of the other axis: the mode must depend on h alone
     dt = 0.4 * h
     j = np.arange(n)
     mode = np.exp(1j * 2 * np.pi * k * j / n)
@@ -92,7 +93,7 @@ def test_euler_entropy_wave_closed_form(phys, axis, k):
     U[1 + axis] = rho * a
     U[3] = p0 / (GAMMA - 1) + 0.5 * rho * a * a
     for _ in range(steps):
-        phys.euler_step(U, dt, h, h, GAMMA, euler.EPS4)
+        phys.euler_step(U, dt, h if axis == 0 else ho, ho if axis == 0 else h, GAMMA, euler.EPS4)
     G = _maccormack_factor(a * dt / h, 2 * np.pi * k / n, euler.EPS4)
     expect = 1.0 + eps * (G ** steps * mode).imag
     got = U[0][0, :] if axis == 0 else U[0][:, 0]
@@ -126,11 +127,15 @@ def test_euler_acoustic_wave_linear_response(phys):
     assert np.max(np.abs((U[0][0] - rho0) - expect)) <= 1e-4 * eps
 
 
-def test_euler_dt_uniform_closed_form(phys):
-    U = _uniform_euler(8, rho=0.5, u=0.4, v=-1.0, p=2.0)
+@pytest.mark.parametrize("u,v,dx,dy", [(0.4, -1.0, 0.1, 0.05), (-2.5, 0.3, 0.04, 0.1)])
+def test_euler_dt_uniform_closed_form(phys, u, v, dx, dy):
+    """dt of a uniform state; the first case is limited along y, the second along x."""
+    U = _uniform_euler(8, rho=0.5, u=u, v=v, p=2.0)
     c = math.sqrt(GAMMA * 2.0 / 0.5)
-    expect = min(0.1 / (0.4 + c), 0.05 / (1.0 + c))
-    assert abs(phys.euler_dt_min(U, 0.1, 0.05, GAMMA) - expect) <= 1e-15 * expect
+    ax, ay = dx / (abs(u) + c), dy / (abs(v) + c)
+    expect = min(ax, ay)
+    assert abs(ax - ay) > 0.05 * expect
+    assert abs(phys.euler_dt_min(U, dx, dy, GAMMA) - expect) <= 1e-15 * expect
 
 
 # ---------------------------------------------------------------- Navier-Stokes
@@ -213,3 +218,104 @@ def test_ns_inviscid_entropy_wave_closed_form(phys, axis):
     expect = 1.0 + eps * (_rk3(z) ** steps * mode).imag
     assert np.max(np.abs(U[0] - expect)) <= 1e-12
     assert np.max(np.abs(U[1 + axis] - a0 * expect)) <= 1e-12
+
+
+# Closed forms of one residual evaluation on anisotropic grids: a sampled sinusoid
+# sin(theta i) along axis a (grid spacing h_a) has D sin = sig cos and D cos = -sig sin
+# exactly, sig = (8 sin theta - sin 2 theta) / (6 h_a); products of sinusoids reduce to
+# sums of harmonics (sin^2 = (1 - cos 2t)/2, sin^3 = (3 sin t - sin 3t)/4, sin cos = sin 2t / 2).
+NS_SHAPE = (8, 10, 12)               # (nz, ny, nx): every axis a different length
+NS_H = (0.55, 0.7, 0.45)             # (hx, hy, hz): every axis a different spacing
+NS_RE, NS_MA, NS_PR = 100.0, 0.1, 0.71
+
+
+def _axis_phase(axis, m=1):
+    K, J, I = np.meshgrid(*[np.arange(s) for s in NS_SHAPE], indexing="ij")
+    n = NS_SHAPE[2 - axis]
+    return 2 * math.pi * m / n, [I, J, K][axis]
+
+
+def _sig(theta, h):
+    return (8 * math.sin(theta) - math.sin(2 * theta)) / (6 * h)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ns_residual_heat_conduction_closed_form(phys, axis):
+    """At rest with uniform pressure and T = 1 + e sin(theta i_a): mass and momentum
+    residuals vanish and the energy residual is the discrete conduction term
+    k D(D T) = -k sig^2 e sin(theta i_a), k = mu / ((gamma - 1) Ma^2 Pr)."""
+    theta, idx = _axis_phase(axis)
+    eps = 0.1
+    T = 1.0 + eps * np.sin(theta * idx)
+    p0 = 1.0 / (GAMMA * NS_MA ** 2)
+    rho = GAMMA * NS_MA ** 2 * p0 / T
+    z = np.zeros(NS_SHAPE)
+    U = _ns_state(rho, z, z, z, np.full(NS_SHAPE, p0))
+    prm = phys.ns_params(GAMMA, NS_MA, NS_RE, NS_PR, NS_H)
+    R = phys.ns_residual(U, prm)
+    kc = (1.0 / NS_RE) / ((GAMMA - 1) * NS_MA ** 2 * NS_PR)
+    expect = -kc * _sig(theta, NS_H[axis]) ** 2 * eps * np.sin(theta * idx)
+    scale = np.max(np.abs(expect))
+    assert np.max(np.abs(R[4] - expect)) <= 1e-12 * scale
+    assert np.max(np.abs(R[:4])) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ns_residual_longitudinal_wave_closed_form(phys, axis):
+    """Uniform density and pressure, velocity u_a = e sin(theta i_a) along its own axis
+    (compressive, so div u and the -2/3 div u part of the stress enter):
+      R_rho = -rho e s1 cos t,
+      R_a   = -rho e^2 s2/2 sin 2t - (4/3) mu e s1^2 sin t,
+      R_E   = -(gamma p/(gamma-1)) e s1 cos t - (rho e^3/8)(3 s1 cos t - s3 cos 3t)
+              + (2/3) mu e^2 s1 s2 cos 2t,
+    s_j = sig(j theta), t = theta i_a; the other momentum residuals vanish."""
+    theta, idx = _axis_phase(axis)
+    h = NS_H[axis]
+    s1, s2, s3 = _sig(theta, h), _sig(2 * theta, h), _sig(3 * theta, h)
+    eps, rho0 = 0.1, 1.0
+    p0 = 1.0 / (GAMMA * NS_MA ** 2)
+    t = theta * idx
+    vel = [np.zeros(NS_SHAPE) for _ in range(3)]
+    vel[axis] = eps * np.sin(t)
+    U = _ns_state(np.full(NS_SHAPE, rho0), vel[0], vel[1], vel[2], np.full(NS_SHAPE, p0))
+    prm = phys.ns_params(GAMMA, NS_MA, NS_RE, NS_PR, NS_H)
+    R = phys.ns_residual(U, prm)
+    mu = 1.0 / NS_RE
+    e_rho = -rho0 * eps * s1 * np.cos(t)
+    e_mom = -rho0 * eps ** 2 * s2 / 2 * np.sin(2 * t) - (4.0 / 3.0) * mu * eps * s1 ** 2 * np.sin(t)
+    e_E = (-(GAMMA * p0 / (GAMMA - 1)) * eps * s1 * np.cos(t)
+           - (rho0 * eps ** 3 / 8) * (3 * s1 * np.cos(t) - s3 * np.cos(3 * t))
+           + (2.0 / 3.0) * mu * eps ** 2 * s1 * s2 * np.cos(2 * t))
+    tol = 1e-12 * np.max(np.abs(e_E))
+    assert np.max(np.abs(R[0] - e_rho)) <= tol
+    assert np.max(np.abs(R[1 + axis] - e_mom)) <= tol
+    assert np.max(np.abs(R[4] - e_E)) <= tol
+    for b in range(3):
+        if b != axis:
+            assert np.max(np.abs(R[1 + b])) <= tol
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ns_residual_pressure_wave_closed_form(phys, axis):
+    """At rest with uniform density and p = p0 + e sin(theta i_a): only the momentum
+    along a feels the pressure, R_a = -e sig cos t; the energy residual is the
+    conduction of T = gamma Ma^2 p / rho, R_E = -k (gamma Ma^2 / rho) sig^2 e sin t."""
+    theta, idx = _axis_phase(axis)
+    sig = _sig(theta, NS_H[axis])
+    eps, rho0 = 0.5, 1.3
+    p0 = 1.0 / (GAMMA * NS_MA ** 2)
+    t = theta * idx
+    z = np.zeros(NS_SHAPE)
+    U = _ns_state(np.full(NS_SHAPE, rho0), z, z, z, p0 + eps * np.sin(t))
+    prm = phys.ns_params(GAMMA, NS_MA, NS_RE, NS_PR, NS_H)
+    R = phys.ns_residual(U, prm)
+    kc = (1.0 / NS_RE) / ((GAMMA - 1) * NS_MA ** 2 * NS_PR)
+    e_mom = -eps * sig * np.cos(t)
+    e_E = -kc * (GAMMA * NS_MA ** 2 / rho0) * sig ** 2 * eps * np.sin(t)
+    tol = 1e-12 * p0
+    assert np.max(np.abs(R[1 + axis] - e_mom)) <= tol
+    assert np.max(np.abs(R[4] - e_E)) <= tol
+    assert np.max(np.abs(R[0])) <= tol
+    for b in range(3):
+        if b != axis:
+            assert np.max(np.abs(R[1 + b])) <= tol

@@ -133,6 +133,38 @@ def test_copy_shift_matches_slicing(oracle_lib):
     assert np.array_equal(fields["d"].a, expect)
 
 
+def test_3d_geometry_matches_slicing(oracle_lib):
+    """3-D datasets whose axes differ in length and in halo depth, each side: a shifted
+    copy and a two-sample LINCOMB equal numpy slicing of the dense arrays (pins the
+    index map of every axis against a library routine)."""
+    size, hlo, hhi = (7, 5, 4), (2, 1, 3), (1, 3, 2)
+    shape = tuple(size[a] + hlo[a] + hhi[a] for a in (2, 1, 0))
+    rng = np.random.default_rng(11)
+    a0, b0 = rng.uniform(-1, 1, size=shape), rng.uniform(-1, 1, size=shape)
+    dats = [DatSpec(nm, size, hlo, hhi, init=v) for nm, v in (("a", a0), ("b", b0))]
+    dats += [DatSpec("c", size, hlo, hhi), DatSpec("d", size, hlo, hhi)]
+    oa, ob = (-2, 1, 2), (1, -1, -2)
+    lo, hi = (0, 0, 0), size
+    c0, c1 = 0.375, -1.25
+    loops = [Loop("copy", lo, hi, [Arg("c", WRITE), Arg("a", READ, [oa])]),
+             Loop("lincomb", lo, hi, [Arg("d", WRITE), Arg("a", READ, [oa]), Arg("b", READ, [ob])],
+                  [0.0, c0, c1])]
+    fields, _ = _run(oracle_lib, dats, [], loops)
+
+    def window(arr, o):
+        # interior points shifted by o (x, y, z); array axes are (z, y, x)
+        return arr[hlo[2] + o[2]:hlo[2] + o[2] + size[2],
+                   hlo[1] + o[1]:hlo[1] + o[1] + size[1],
+                   hlo[0] + o[0]:hlo[0] + o[0] + size[0]]
+
+    ec = np.zeros(shape)
+    window(ec, (0, 0, 0))[...] = window(a0, oa)
+    assert np.array_equal(fields["c"].a, ec)
+    ed = np.zeros(shape)
+    window(ed, (0, 0, 0))[...] = c0 * window(a0, oa) + c1 * window(b0, ob)
+    assert np.array_equal(fields["d"].a, ed)
+
+
 def test_chain_program_order(oracle_lib):
     """Two loops that each shift by one point compose to a shift by two (a later loop
     sees the earlier loop's writes)."""
