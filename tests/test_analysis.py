@@ -135,9 +135,10 @@ def test_write_first_and_read_only_copies(lib):
     downloaded either."""
     n = 32
     dats = [DatSpec("a", (n, n), (1, 1), (1, 1)), DatSpec("t", (n, n), (0, 1), (0, 1)),
-            DatSpec("b", (n, n), (1, 1), (1, 1))]
+            DatSpec("b", (n, n), (1, 1), (1, 1)), DatSpec("c", (n, n), (2, 1), (2, 1))]
     loops = [Loop("copy", (0, 0), (n, n), [Arg("t", WRITE), Arg("a", READ, [(0, 1)])]),
-             Loop("lincomb", (0, 0), (n, n), [Arg("b", WRITE), Arg("t", READ, [(0, 0), (0, -1)])], [0.0, 0.5, 0.5])]
+             Loop("lincomb", (0, 0), (n, n), [Arg("b", WRITE), Arg("t", READ, [(0, 0), (0, -1)])], [0.0, 0.5, 0.5]),
+             Loop("copy", (-1, 0), (n, n), [Arg("c", WRITE), Arg("a", READ, [(0, 1)])])]
     for flags, t_down in ((0, True), (oc.OC_FLAG_CYCLIC, False)):
         plan, _, names = dry(1 << 30, dats, [], loops, h=8, depth=3, flags=flags)
         by = {d["dat"]: d for d in plan["dats"]}
@@ -149,6 +150,10 @@ def test_write_first_and_read_only_copies(lib):
         # b is first written over its interior columns: only its halo columns travel
         assert len(b["up"]) > 0 and all(x0 == 0 and x1 == n for _, _, _, x0, x1 in b["up"])
         assert (len(b["down"]) > 0) == t_down
+        # c is first written over x in [-1, n), one column into its low halo: only the
+        # columns outside that strip travel
+        c = by[names["c"]]
+        assert len(c["up"]) > 0 and all(x0 == -1 and x1 == n for _, _, _, x0, x1 in c["up"])
 
 
 @pytest.mark.parametrize("bad", ["write_offset", "extent", "self_read", "lincomb_params", "mixed_dtype"])

@@ -11,6 +11,7 @@ oracle's own output and would catch any change trivially.
 
 The mistakes are planted on the CPU only; nothing here touches the CUDA path.
 """
+import concurrent.futures as cf
 import os
 import subprocess
 import sys
@@ -228,33 +229,55 @@ def _build_mutant(tmp, fname, old, new):
 
 
 def _run_pins(pins, lib):
-    env = dict(os.environ, ORACLE_LIB=lib, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    env = dict(os.environ, ORACLE_LIB=lib, OMP_NUM_THREADS="1")
     return subprocess.run([sys.executable, "-m", "pytest", pins, "-x", "-q", "-p", "no:cacheprovider",
                            "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
-def test_unmutated_copy_passes_the_pins(tmp_path):
-    """The harness itself: the unchanged source, built the same way, passes every pin."""
-    so = _build_mutant(str(tmp_path), "", "", "")
-    for pins in sorted(set(PINS.values())):
+def _c_case(tmp, fname, old, new):
+    so = _build_mutant(tmp, fname, old, new)
+    files = [PINS[fname]] if fname else sorted(set(PINS.values()))
+    rcs, out = [], ""
+    for pins in files:
         r = _run_pins(pins, so)
-        assert r.returncode == 0, r.stdout[-2000:]
+        rcs.append(r.returncode)
+        out += r.stdout[-1500:]
+    return max(rcs), out
 
 
-def test_unmutated_mlp_copy_passes_the_pins(tmp_path):
-    r = _run_mlp_pins(str(tmp_path), "", "")
-    assert r.returncode == 0, r.stdout[-2000:]
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """(exit status, output tail) of every case, keyed by id; the cases are independent
+    subprocesses and run concurrently."""
+    jobs = {"c_unmutated": (_c_case, "", "", ""), "mlp_unmutated": (_run_mlp_pins, "", "")}
+    for mid, fname, old, new in MUTANTS:
+        jobs[mid] = (_c_case, fname, old, new)
+    for mid, old, new in MLP_MUTANTS:
+        jobs[mid] = (_run_mlp_pins, old, new)
+
+    base = tmp_path_factory.mktemp("mutants")
+
+    def run(item):
+        mid, (fn, *args) = item
+        tmp = os.path.join(str(base), mid)
+        os.makedirs(tmp)
+        r = fn(tmp, *args)
+        return mid, (r if isinstance(r, tuple) else (r.returncode, r.stdout[-1500:]))
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        return dict(ex.map(run, jobs.items()))
 
 
-@pytest.mark.parametrize("mid,old,new", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
-def test_pins_catch_mlp_mutant(tmp_path, mid, old, new):
-    r = _run_mlp_pins(str(tmp_path), old, new)
-    assert r.returncode == 1, f"mutant {mid} survived the pins:\n{r.stdout[-1500:]}"
+def test_unmutated_copies_pass_the_pins(outcomes):
+    """The harness itself: the unchanged sources, built and loaded the same way, pass
+    every pin."""
+    for mid in ("c_unmutated", "mlp_unmutated"):
+        rc, out = outcomes[mid]
+        assert rc == 0, out
 
 
-@pytest.mark.parametrize("mid,fname,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_mutant(tmp_path, mid, fname, old, new):
-    so = _build_mutant(str(tmp_path), fname, old, new)
-    r = _run_pins(PINS[fname], so)
+@pytest.mark.parametrize("mid", [m[0] for m in MUTANTS] + [m[0] for m in MLP_MUTANTS])
+def test_pins_catch_mutant(outcomes, mid):
+    rc, out = outcomes[mid]
     # exit status 1: a test failed (not a collection or usage error)
-    assert r.returncode == 1, f"mutant {mid} survived the pins:\n{r.stdout[-1500:]}"
+    assert rc == 1, f"mutant {mid} survived the pins:\n{out}"
