@@ -237,6 +237,31 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
             return step
         fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)
         return dats, [], make_step, fp, n ** 3 * spc
+    if name == "clover3d":
+        # one step = SUMMARY_EVERY time steps (one chain each, ended by the MIN the user
+        # reads) followed by the read-only summary chain, the cadence of Sec. 5.3
+        from workloads import clover3d
+        dats = clover3d.datasets(n, n, "f32" if mixed else "f64")
+        if mixed:
+            for d in dats:
+                d.init = d.init.astype(np.float32)
+        sreds, sloops = clover3d.step_chain(n, n)
+        mreds, mloops = clover3d.summary_chain(n, n)
+
+        def make_step(ex):
+            def step():
+                out = []
+                for _ in range(clover3d.SUMMARY_EVERY):
+                    for lp in sloops:
+                        ex.enqueue(lp)
+                    out.append(ex.reduce("dt"))
+                for lp in mloops:
+                    ex.enqueue(lp)
+                out += [ex.reduce(r.name) for r in mreds]
+                return out
+            return step
+        fp = clover3d.footprint_bytes(n, n, 4 if mixed else 8)
+        return dats, sreds + mreds, make_step, fp, n ** 3 * clover3d.SUMMARY_EVERY
     raise ValueError(name)
 
 
@@ -333,7 +358,8 @@ def reference_main(args):
         return 0
     if args.workload != "random":
         print(json.dumps({"impl": "reference", "unavailable": "the CPU reference leg times the random-chain "
-                          "workload; the PDE workloads have oracle step functions but no timed leg"}))
+                          "workload; the other workloads are checked against the oracle in the tests but "
+                          "have no timed leg"}))
         return 0
     import oracle
     from workloads import random_chain
@@ -398,6 +424,10 @@ WORKLOADS = {
     "tgv": ("3-D compressible Navier-Stokes Taylor-Green vortex (4th-order central, low-storage RK3), "
             "{nd} datasets, {spc} RK3 step(s) per chain, device budget 1/3 of the footprint",
             ("ns_prim", "ns_grad", "ns_flux", "ns_div", "ns_update", "hilo_add"), 640),
+    "clover3d": ("CloverLeaf-3D-like chains: {nd} datasets on an n^3 grid (halo 2); one step = 10 time "
+                 "steps of 599 LINCOMB loops sweeping x, y, z (each ended by a MIN the user reads) plus a "
+                 "read-only summary chain of 12 reductions; device budget 1/3 of the footprint",
+                 ("lincomb", "reduce"), 256),
 }
 
 

@@ -1,10 +1,12 @@
 """Host logic of bench.py that needs no GPU: the clock-sample summary (which decides
 whether a run is kept), the peak denominators, the recorded-traffic lookup (which must
-drop a capture once the kernel it describes has changed) and the kernel names."""
+drop a capture once the kernel it describes has changed), the kernel names and the step
+structure of a workload."""
 import hashlib
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
@@ -96,3 +98,38 @@ def test_committed_traffic_record_points_at_real_markers():
         text = open(os.path.join(bench.ROOT, "paper_1709_02125_gb300", "csrc", rec["source"])).read()
         a, b = text.find(rec["from"]), text.find(rec["to"])
         assert 0 <= a < b, key
+
+
+class _FakeExecutor:
+    """Records what a bench step enqueues and reads (no library, no GPU)."""
+
+    def __init__(self):
+        self.enqueued, self.reads = [], []
+
+    def enqueue(self, lp):
+        self.enqueued.append(lp)
+
+    def reduce(self, name):
+        self.reads.append((len(self.enqueued), name))
+        return 0.0
+
+    def flush(self):
+        self.reads.append((len(self.enqueued), None))
+
+
+def test_clover3d_bench_step_structure():
+    """One bench step of the CloverLeaf-3D-like workload: 10 time-step chains of 599
+    loops, each ended by reading its MIN, then the 12-reduction summary chain."""
+    from workloads import clover3d
+    dats, reds, make_step, fp, ct = bench.build_workload("clover3d", False, 8)
+    assert len(dats) == 30 and fp == clover3d.footprint_bytes(8, 8, 8) and ct == 8 ** 3 * 10
+    assert {r.name for r in reds} == {"dt"} | {f"sm{i}" for i in range(12)}
+    ex = _FakeExecutor()
+    out = make_step(ex)()
+    assert len(out) == 10 + 12
+    assert len(ex.enqueued) == 10 * 599 + 12
+    dt_reads = [k for k, nm in ex.reads if nm == "dt"]
+    assert dt_reads == [599 * (i + 1) for i in range(10)]
+    assert [nm for _, nm in ex.reads[10:]] == [f"sm{i}" for i in range(12)]
+    mixed = bench.build_workload("clover3d", True, 8)
+    assert all(d.dtype == "f32" and d.init.dtype == np.float32 for d in mixed[0])
