@@ -46,7 +46,7 @@ extern "C" {
 #define OC_ERR_ARG      -1  /* invalid argument, handle, range or stencil          */
 #define OC_ERR_BUDGET   -2  /* the device budget cannot hold one tile of the chain  */
 #define OC_ERR_CUDA     -3  /* a CUDA runtime call failed (message has the reason)  */
-#define OC_ERR_TIMEOUT  -4  /* a bounded wait on a stream or event expired          */
+#define OC_ERR_TIMEOUT  -4  /* a bounded wait on a stream or event expired (below)  */
 #define OC_ERR_STATE    -5  /* call out of order (no context, double init, ...)     */
 #define OC_ERR_NOMEM    -6  /* host (pinned) allocation failed                      */
 
@@ -184,7 +184,8 @@ typedef struct oc_stats_t {
  *                       into the compute stream before anything else waits on it.
  *  flags                OC_FLAG_* bits.  planner_mode: OC_PLAN_*.
  * Errors: OC_ERR_STATE if a context exists; OC_ERR_ARG on an arena smaller than
- * the budget; OC_ERR_CUDA if the device cannot be used (not with OC_FLAG_DRYRUN). */
+ * the budget, arena_bytes without an arena, or an unknown planner mode; OC_ERR_CUDA if
+ * the device cannot be used (not with OC_FLAG_DRYRUN). */
 int oc_init(size_t device_budget_bytes, void* device_arena, size_t arena_bytes,
             void* const streams[3], uint32_t flags, int planner_mode);
 
@@ -219,7 +220,11 @@ int oc_enqueue_loop(int kernel_id, const int range_lo[3], const int range_hi[3],
                     int nargs, const oc_arg* args, const double* params, int nparams);
 
 /* Execute the queued chain (Sec. 3: a call returning data ends the chain; Sec. 4
- * Algorithm 1 streams its tiles). Returns when every result is in host memory. */
+ * Algorithm 1 streams its tiles). Returns when every result is in host memory.
+ * Every host wait on the device (here, in oc_reduce and in oc_fetch_dat) is bounded:
+ * 600 s, or the number of seconds in the environment variable OC_TIMEOUT_S when
+ * oc_init ran. On expiry the call returns OC_ERR_TIMEOUT with the device work still
+ * queued; the context is then in an unknown state and should be finalized. */
 int oc_flush(void);
 
 /* Flush, then return the value of reduction `red` of the last chain that named it. */

@@ -46,6 +46,16 @@ def test_second_context_is_refused(dry):
     assert "already exists" in _err(dry)
 
 
+def test_init_argument_errors(L):
+    ptrs = (ctypes.c_void_p * 3)()
+    D = oc.OC_FLAG_DRYRUN
+    assert L.oc_init(1 << 20, None, 0, ptrs, D, 7) == oc.OC_ERR_ARG             # planner mode
+    assert L.oc_init(1 << 20, None, 4096, ptrs, D, 0) == oc.OC_ERR_ARG          # bytes, no arena
+    buf = ctypes.create_string_buffer(16)
+    assert L.oc_init(1 << 20, ctypes.addressof(buf), 16, ptrs, D, 0) == oc.OC_ERR_ARG  # arena < budget
+    assert L.oc_flush() == oc.OC_ERR_STATE                                    # none was created
+
+
 def test_init_without_a_device_is_a_cuda_error(L):
     """Without OC_FLAG_DRYRUN the context needs a device; on a machine without one the
     call fails cleanly with OC_ERR_CUDA and leaves no context behind."""
