@@ -217,3 +217,35 @@ def test_prefetch_simulation_matches_oracle(lib, oracle_lib, seed, h, depth):
         assert np.array_equal(got[d.name].a, ref[d.name].a), d.name
     for r in reds:
         assert abs(gred[r.name] - rred[r.name]) <= 1e-12 * max(1.0, abs(rred[r.name]))
+
+
+@pytest.mark.parametrize("nd,dtype", [(2, "f64"), (3, "f32")])
+def test_planner_features_of_a_chain(lib, nd, dtype):
+    """The 8 planner features (include/oc.h) of a planned chain, from the chain's own
+    description: log2 loops, datasets used, slow-axis radius, bytes per cell summed over
+    the datasets used, budget over footprint, dimensions, log2 footprint, log2 slow rows.
+    (Features are taken when a chain is planned out of core, so the budget is a third of
+    the footprint.)"""
+    n, nz = (200, None) if nd == 2 else (24, 160)
+    dats, reds, loops = random_chain.build_general(nd, n, 9, 14, 2, seed=77, dtype=dtype, nz=nz)
+    esz = 8 if dtype == "f64" else 4
+    budget = sum(int(np.prod(d.shape)) * esz for d in dats) // 3
+    with oc.Executor(budget, dryrun=True) as ex:
+        oc.run_chain(ex, dats, reds, loops)
+        f = ex.features()
+        assert ex.stats()["tiles"] > 1
+    used = {a.name for lp in loops for a in lp.args if a.access != "red"}
+    sa = nd - 1
+    radius = max(abs((tuple(o) + (0, 0))[sa]) for lp in loops for a in lp.args if a.access == "r" for o in a.offsets)
+    fp = sum(int(np.prod(d.shape)) * esz for d in dats if d.name in used)
+    slow = max(lp.hi[sa] for lp in loops) - min(lp.lo[sa] for lp in loops)
+    assert f[0] == pytest.approx(np.log2(len(loops)), abs=1e-6)
+    assert f[1] == len(used)
+    assert f[2] == radius
+    assert f[3] == len(used) * esz
+    # the library counts its padded rows (x-lines rounded up to 128 bytes): between the
+    # dense footprint and 1.25 times it at these widths
+    assert budget / fp / 1.25 <= f[4] <= budget / fp * (1 + 1e-6)
+    assert f[5] == nd
+    assert np.log2(fp) - 1e-6 <= f[6] <= np.log2(1.25 * fp)
+    assert f[7] == pytest.approx(np.log2(slow), abs=1e-6)
