@@ -49,20 +49,28 @@ def sample_chain(rng, min_gb, max_gb):
     return dict(nd=nd, F=F, L=L, radius=radius, dtype=dtype, n=n, nz=nz, ratio=ratio, seed=seed)
 
 
-def run_one(c, flags):
+def run_one(c, flags, repeats=1):
+    """Autotune the chain `repeats` times, each on a fresh context; the first table is
+    `table`, all of them `tables` (when repeats > 1), so that the timing noise between
+    candidates can be measured and averaged out."""
     dats, reds, loops = random_chain.build_general(c["nd"], c["n"], c["F"], c["L"], c["radius"], c["seed"],
                                                    c["dtype"], c["nz"])
     fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)
     budget = int(fp * c["ratio"])
-    with oc.Executor(budget, flags=flags, planner=oc.OC_PLAN_AUTOTUNE) as ex:
-        oc.run_chain(ex, dats, reds, loops, flush=False)
-        t0 = time.perf_counter()
-        ex.flush()
-        tune_s = time.perf_counter() - t0
-        table = ex.autotune_result()
-        feats = ex.features()
-    return dict(config=c, footprint=fp, budget=budget, features=[float(v) for v in feats],
-                table=table.tolist(), tune_seconds=tune_s)
+    tables, tune_s = [], 0.0
+    for _ in range(repeats):
+        with oc.Executor(budget, flags=flags, planner=oc.OC_PLAN_AUTOTUNE) as ex:
+            oc.run_chain(ex, dats, reds, loops, flush=False)
+            t0 = time.perf_counter()
+            ex.flush()
+            tune_s += time.perf_counter() - t0
+            tables.append(ex.autotune_result().tolist())
+            feats = ex.features()
+    row = dict(config=c, footprint=fp, budget=budget, features=[float(v) for v in feats],
+               table=tables[0], tune_seconds=tune_s)
+    if repeats > 1:
+        row["tables"] = tables
+    return row
 
 
 def main():
@@ -73,6 +81,7 @@ def main():
     ap.add_argument("--max-gb", type=float, default=8.0)
     ap.add_argument("--out", required=True)
     ap.add_argument("--time-limit-s", type=float, default=1e9)
+    ap.add_argument("--repeats", type=int, default=1, help="autotune runs per chain (timing noise)")
     args = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
@@ -83,7 +92,7 @@ def main():
         for i in range(args.count):
             c = sample_chain(rng, args.min_gb, args.max_gb)
             try:
-                row = run_one(c, flags)
+                row = run_one(c, flags, args.repeats)
             except oc.OcError as e:   # a budget that cannot hold one tile: skip the sample
                 print(f"sample {i}: {e}", flush=True)
                 continue

@@ -33,6 +33,8 @@ FIXED = (0, 3)   # grid index 0 (largest fitting height), depth 3
 
 
 def load_rows(path):
+    """Sweep rows with `table` as an array. A row autotuned several times (`tables`) gets
+    the per-candidate median of its timings."""
     rows = []
     with open(path) as f:
         for line in f:
@@ -40,6 +42,11 @@ def load_rows(path):
             t = np.array(r["table"], dtype=np.float64)
             if len(t) == 0:
                 continue
+            if "tables" in r:
+                reps = [np.array(x, dtype=np.float64) for x in r["tables"]]
+                if all(x.shape == t.shape and np.array_equal(x[:, [0, 1, 3]], t[:, [0, 1, 3]]) for x in reps):
+                    t = t.copy()
+                    t[:, 2] = np.median(np.stack([x[:, 2] for x in reps]), axis=0)
             r["table"] = t
             rows.append(r)
     return rows
