@@ -133,3 +133,21 @@ def test_clover3d_bench_step_structure():
     assert [nm for _, nm in ex.reads[10:]] == [f"sm{i}" for i in range(12)]
     mixed = bench.build_workload("clover3d", True, 8)
     assert all(d.dtype == "f32" and d.init.dtype == np.float32 for d in mixed[0])
+
+
+def test_cpu_baseline_reports_threads_used_and_model(oracle_lib):
+    """The CPU baseline states the threads the oracle really used (one on a 2-D chain:
+    its OpenMP loops run over the third axis) beside those available, and the CPU model."""
+    b = bench.cpu_baseline(64, budget_s=0.2)
+    assert b["kind"] == "oracle" and b["value"] > 0
+    assert b["cores"] == 1 and b["threads_available"] >= 1
+    assert isinstance(b["cpu_model"], str) and b["cpu_model"]
+
+
+def test_oracle_cores_used():
+    from workloads import random_chain
+    _, _, loops2 = random_chain.build_general(2, 16, 4, 4, 1, seed=1)
+    _, _, loops3 = random_chain.build_general(3, 8, 4, 4, 1, seed=1, nz=5)
+    assert bench.oracle_cores_used(loops2, 16) == 1
+    assert bench.oracle_cores_used(loops3, 16) == 5
+    assert bench.oracle_cores_used(loops3, 3) == 3
