@@ -8,7 +8,8 @@ It implements the sequential meaning of a chain (arXiv 1709.02125, Sec. 3): loop
 one after another in program order over their whole iteration ranges, on full arrays
 held in host memory; each kernel is evaluated pointwise as defined in `oracle.c`.
 The PDE workloads (Euler, Navier-Stokes) have their own step functions in
-`oracle.physics`, written with plain periodic (modular) indexing.
+`oracle.physics`, written with plain periodic (modular) indexing, and a loop-level form
+of the same arithmetic in `oracle.physics_loops` (pinned to the step functions).
 """
 from __future__ import annotations
 
@@ -107,8 +108,11 @@ def _o3(offs, nd):
 
 def run_loop(loop, fields: Dict[str, Field], reds: Dict[str, float], red_ops: Dict[str, str]):
     """Evaluate one loop (a `workloads.spec.Loop`) in place on `fields`."""
-    L = lib()
     k = loop.kernel
+    if k.startswith("euler_") or k.startswith("ns_"):
+        from . import physics_loops
+        return physics_loops.run_loop(loop, fields, reds, red_ops)
+    L = lib()
     args = loop.args
     dst = fields[args[0].name] if args[0].access in ("w", "rw") else None
     nd = (dst or fields[args[0].name]).ndim
@@ -149,11 +153,16 @@ def run_loop(loop, fields: Dict[str, Field], reds: Dict[str, float], red_ops: Di
         else:
             reds[red] = min(reds[red], v)
     else:
-        raise NotImplementedError(f"kernel {k!r}: the PDE workloads are defined by oracle.physics step functions")
+        raise NotImplementedError(f"kernel {k!r}")
 
 
 def make_fields(dats) -> Dict[str, Field]:
-    return {d.name: Field(d.size, d.halo_lo, d.halo_hi, d.init) for d in dats}
+    out = {}
+    for d in dats:
+        f = Field(d.size, d.halo_lo, d.halo_hi, d.init)
+        f.periodic = tuple(getattr(d, "periodic", ()))
+        out[d.name] = f
+    return out
 
 
 def run_chain(loops: List, fields: Dict[str, Field], red_specs) -> Dict[str, float]:

@@ -99,7 +99,7 @@ def check_legality(plan, loops):
 
 
 def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int], chains: int = 1,
-             prefetch: bool = False, stats: Dict = None):
+             prefetch: bool = False, stats: Dict = None, chain_start=None):
     """Replay the plan with tagged cyclic slabs for `chains` repetitions of the chain;
     returns (fields, reductions of the last chain).
 
@@ -108,7 +108,10 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int], chains:
     all sit in slots not used by rows live in phases T - 1 and T, and none of which is
     downloaded in those phases, has those rows copied from the host into its slab; the
     next chain skips them. The simulation checks that the prefetched slots stay untouched
-    until the next chain reads them."""
+    until the next chain reads them.
+
+    `chain_start(host)`, if given, runs on the host fields before each chain's first copy
+    (the executor refreshes the deep ghost rows of periodic datasets there)."""
     T, k = plan["tiles"], plan["depth"] - 2
     by_handle = {d["dat"]: d for d in plan["dats"]}
     specs = {d.name: d for d in dats}
@@ -186,6 +189,8 @@ def simulate(plan, loops, dats, reds, oracle, handle_of: Dict[str, int], chains:
     have = {}   # rows prefetched for the next chain, per dataset
     for c in range(chains):
         red_vals = {}
+        if chain_start is not None:
+            chain_start(host)
         have = _run_chain(plan, loops, T, k, slabs, host, specs, red_ops, red_vals, oracle, slot, phase_rows,
                           upload_row, have, prefetch and c + 1 < chains, prefetch_rows, stats)
     return host, red_vals
