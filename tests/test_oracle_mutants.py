@@ -4,9 +4,9 @@ Each case plants one plausible mistake in a copy of the oracle's source (a dropp
 term, a wrong sign, index, axis or coefficient, a transposed operand) and runs the
 independent pins against that copy: for the C library (built into a temporary library
 and loaded through ORACLE_LIB) test_oracle_pins.py for the loop kernels and
-test_oracle_physics.py for the PDE step functions; for the planner network's numpy
-oracle (the mutated module stands in for oracle.mlp) test_oracle_mlp.py. The pins must
-fail for every mutant. The golden fixtures are left out on purpose: they are the
+test_oracle_physics.py for the PDE step functions; for the numpy modules (the mutated
+module stands in for oracle.mlp or oracle.physics_loops) test_oracle_mlp.py and the
+step-equality tests of test_physics_loops.py. The pins must fail for every mutant. The golden fixtures are left out on purpose: they are the
 oracle's own output and would catch any change trivially.
 
 The mistakes are planted on the CPU only; nothing here touches the CUDA path.
@@ -185,30 +185,65 @@ MLP_MUTANTS = [
     ("mlp_adam_sign", "return p - lr * mh", "return p + lr * mh"),
 ]
 
-_MLP_RUNNER = """
+# loop-level PDE oracle (oracle/physics_loops.py), pinned bit for bit to the whole-step
+# functions by the "equals" tests of test_physics_loops.py
+LOOP_MUTANTS = [
+    ("loops_euler_pressure_term", "p = (gamma - 1.0) * (E - 0.5 * (mx * u + my * v))",
+     "p = (gamma - 1.0) * (E - 0.5 * (mx * u))"),
+    ("loops_euler_flux_pressure", "Fv = (mx, mx * u + p, mx * v, (E + p) * u)", "Fv = (mx, mx * u, mx * v, (E + p) * u)"),
+    ("loops_euler_pred_sign", "(U - lx * dF) - ly * dG", "(U - lx * dF) + ly * dG"),
+    ("loops_euler_corr_d4", "((m2 - 4.0 * m1) + 6.0 * U)", "((m2 - 4.0 * m1) + 5.0 * U)"),
+    ("loops_euler_corr_backward", "_get(g[8 + c], lo, hi, (-1, 0))", "_get(g[8 + c], lo, hi, (1, 0))"),
+    ("loops_euler_corr_state", "first = (U + S) if mode == 0.0", "first = (S + S) if mode == 0.0"),
+    ("loops_euler_dt_gamma", "c = np.sqrt(gamma * p / rho)", "c = np.sqrt(p / rho)"),
+    ("loops_ns_temperature", "T = gamma * Ma * Ma * p / rho", "T = Ma * Ma * p / rho"),
+    ("loops_ns_divergence", "div = (D[0] + D[4]) + D[8]", "div = D[0] + D[4]"),
+    ("loops_ns_heat_flux_sign", "- kc * D[9 + a]", "+ kc * D[9 + a]"),
+    ("loops_d1_coefficient", "((fm2 - 8.0 * fm1) + (8.0 * fp1 - fp2)) / (12.0 * h)",
+     "((fm2 - 6.0 * fm1) + (6.0 * fp1 - fp2)) / (12.0 * h)"),
+    ("loops_rk_register", "Acoef * _get(out, lo, hi) + dt * r", "_get(out, lo, hi) + dt * r"),
+    ("loops_rk_update", "_get(g[m], lo, hi) + B * _get(g[5 + m], lo, hi)", "_get(g[m], lo, hi) + _get(g[5 + m], lo, hi)"),
+    ("loops_fast_axis_wrap", "r = np.mod(r, f.size[a])", "r = np.clip(r, 0, f.size[a] - 1)"),
+    ("loops_ghost_rows", "f.a[r] = f.a[(y % n) + h0]", "f.a[r] = f.a[min(max(y, 0), n - 1) + h0]"),
+]
+
+_PY_RUNNER = """
 import importlib.util, sys
 sys.path[:0] = [{root!r}, {tests!r}]
 import oracle
-spec = importlib.util.spec_from_file_location("oracle.mlp", {path!r})
+spec = importlib.util.spec_from_file_location("oracle.{mod}", {path!r})
 mod = importlib.util.module_from_spec(spec)
 spec.loader.exec_module(mod)
-sys.modules["oracle.mlp"] = mod
-oracle.mlp = mod
+sys.modules["oracle.{mod}"] = mod
+setattr(oracle, {mod!r}, mod)
 import pytest
-sys.exit(pytest.main(["tests/test_oracle_mlp.py", "-x", "-q", "-p", "no:cacheprovider"]))
+sys.exit(pytest.main({pins!r} + ["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
 """
+
+PY_PINS = {"mlp": ["tests/test_oracle_mlp.py"], "physics_loops": ["tests/test_physics_loops.py", "-k", "equals"]}
+
+
+def _run_py_pins(tmp, module, old, new):
+    """Run the pins of the numpy oracle module `module` with a mutated copy standing in
+    for it."""
+    text = open(os.path.join(ORACLE, module + ".py")).read()
+    if old:
+        assert text.count(old) == 1, f"mutant text must occur once in {module}.py: {old!r}"
+        text = text.replace(old, new)
+    path = os.path.join(tmp, module + "_mutant.py")
+    with open(path, "w") as fh:
+        fh.write(text)
+    code = _PY_RUNNER.format(root=ROOT, tests=os.path.join(ROOT, "tests"), mod=module, path=path,
+                             pins=PY_PINS[module])
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
 
 
 def _run_mlp_pins(tmp, old, new):
-    text = open(os.path.join(ORACLE, "mlp.py")).read()
-    if old:
-        assert text.count(old) == 1, f"mutant text must occur once in mlp.py: {old!r}"
-        text = text.replace(old, new)
-    path = os.path.join(tmp, "mlp_mutant.py")
-    with open(path, "w") as fh:
-        fh.write(text)
-    code = _MLP_RUNNER.format(root=ROOT, tests=os.path.join(ROOT, "tests"), path=path)
-    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return _run_py_pins(tmp, "mlp", old, new)
+
+
+def _run_loop_pins(tmp, old, new):
+    return _run_py_pins(tmp, "physics_loops", old, new)
 
 
 def _build_mutant(tmp, fname, old, new):
@@ -249,7 +284,10 @@ def _c_case(tmp, fname, old, new):
 def outcomes(tmp_path_factory):
     """(exit status, output tail) of every case, keyed by id; the cases are independent
     subprocesses and run concurrently."""
-    jobs = {"c_unmutated": (_c_case, "", "", ""), "mlp_unmutated": (_run_mlp_pins, "", "")}
+    jobs = {"c_unmutated": (_c_case, "", "", ""), "mlp_unmutated": (_run_mlp_pins, "", ""),
+            "loops_unmutated": (_run_loop_pins, "", "")}
+    for mid, old, new in LOOP_MUTANTS:
+        jobs[mid] = (_run_loop_pins, old, new)
     for mid, fname, old, new in MUTANTS:
         jobs[mid] = (_c_case, fname, old, new)
     for mid, old, new in MLP_MUTANTS:
@@ -271,12 +309,12 @@ def outcomes(tmp_path_factory):
 def test_unmutated_copies_pass_the_pins(outcomes):
     """The harness itself: the unchanged sources, built and loaded the same way, pass
     every pin."""
-    for mid in ("c_unmutated", "mlp_unmutated"):
+    for mid in ("c_unmutated", "mlp_unmutated", "loops_unmutated"):
         rc, out = outcomes[mid]
         assert rc == 0, out
 
 
-@pytest.mark.parametrize("mid", [m[0] for m in MUTANTS] + [m[0] for m in MLP_MUTANTS])
+@pytest.mark.parametrize("mid", [m[0] for m in MUTANTS] + [m[0] for m in MLP_MUTANTS] + [m[0] for m in LOOP_MUTANTS])
 def test_pins_catch_mutant(outcomes, mid):
     rc, out = outcomes[mid]
     # exit status 1: a test failed (not a collection or usage error)
