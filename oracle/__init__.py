@@ -54,15 +54,34 @@ def lib():
         P, I = ctypes.c_void_p, ctypes.c_int
         L.or_copy.argtypes = [P, P, P, P, P, P, P]
         L.or_lincomb.argtypes = [P, P, P, P, I, P, P, P, P, P, ctypes.c_double]
+        L.or_lincomb.restype = I
         L.or_reduce.argtypes = [P, P, P, P, P, P, I, I]
         L.or_reduce.restype = ctypes.c_double
         L.or_threads.restype = I
+        L.or_set_threads.argtypes = [I]
+        L.or_set_threads.restype = None
         _lib = L
     return _lib
 
 
 def threads() -> int:
     return int(lib().or_threads())
+
+
+def _default_threads() -> int:
+    import os as _os
+    try:
+        return max(1, int(_os.environ.get("OMP_NUM_THREADS", "")))
+    except ValueError:
+        return max(1, _os.cpu_count() or 1)
+
+
+threads_default = _default_threads()
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's OpenMP loops on n threads from now on (results do not depend on it)."""
+    lib().or_set_threads(int(n))
 
 
 def _ip(a):
@@ -131,10 +150,12 @@ def run_loop(loop, fields: Dict[str, Field], reds: Dict[str, float], red_ops: Di
         npts = np.array([len(a.offsets) for a in args[1:]], dtype=np.int32)
         offs = np.array([o for a in args[1:] for o in _o3(a.offsets, nd)], dtype=np.int32).reshape(-1)
         coef = np.array(loop.params[1:], dtype=np.float64)
-        if len(coef) != int(npts.sum()):
-            raise ValueError("lincomb: one coefficient per sample")
-        L.or_lincomb(_ip(lo3), _ip(hi3), _ip(dst.a), _ip(dst.geo), len(ins), ptrs, _ip(geos),
-                     _ip(npts), _ip(offs), _ip(coef), float(loop.params[0]))
+        if len(coef) != int(npts.sum()) or len(coef) < 1:
+            raise ValueError("lincomb: one coefficient per sample, at least one sample")
+        rc = L.or_lincomb(_ip(lo3), _ip(hi3), _ip(dst.a), _ip(dst.geo), len(ins), ptrs, _ip(geos),
+                          _ip(npts), _ip(offs), _ip(coef), float(loop.params[0]))
+        if rc != 0:
+            raise MemoryError(f"or_lincomb failed ({rc})")
     elif k == "reduce":
         srcs = [a for a in args if a.access == "r"]
         red = [a for a in args if a.access == "red"][0].name

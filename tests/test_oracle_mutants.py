@@ -59,10 +59,12 @@ MUTANTS = [
     ("reduce_min_is_max", "oracle.c",
      "else m = v < m ? v : m;", "else m = v > m ? v : m;"),
     ("reduce_rows_skipped", "oracle.c",
-     "for (int k = 0; k < nz; ++k) {", "for (int k = 1; k < nz; ++k) {"),
+     "for (k = 0; k < nr; ++k) {\n        if (op == 0)", "for (k = 1; k < nr; ++k) {\n        if (op == 0)"),
     ("reduce_row_range", "oracle.c",
-     "for (int y = lo[1]; y < hi[1]; ++y)\n            for (int x = lo[0]; x < hi[0]; ++x) {\n                double v",
-     "for (int y = lo[1]; y < hi[1]; ++y)\n            for (int x = lo[0] + 1; x < hi[0]; ++x) {\n                double v"),
+     "for (int x = lo[0]; x < hi[0]; ++x) {\n                    double v",
+     "for (int x = lo[0] + 1; x < hi[0]; ++x) {\n                    double v"),
+    ("reduce_row_split_overlap", "oracle.c",
+     "y1 = three ? hi[1] : r0 + k + 1;", "y1 = three ? hi[1] : r0 + k + 2;"),
     # ---- Euler (Sec. 5.1 stand-in: MacCormack with fourth-order dissipation)
     ("euler_pressure_dropped_term", "physics.c",
      "double p = (gamma - 1.0) * (E[q] - 0.5 * (mx[q] * u + my[q] * v));",

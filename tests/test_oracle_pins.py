@@ -204,3 +204,54 @@ def test_out_of_extent_access_rejected(oracle_lib):
     dats = [DatSpec("a", (n, n), (1, 1), (1, 1)), DatSpec("b", (n, n), (1, 1), (1, 1))]
     with pytest.raises(IndexError):
         _run(oracle_lib, dats, [], [Loop("copy", (0, 0), (n, n), [Arg("b", WRITE), Arg("a", READ, [(2, 0)])])])
+
+
+@pytest.mark.parametrize("nin,per", [(5, 13), (4, 25)])
+def test_lincomb_more_than_64_samples(oracle_lib, nin, per):
+    """65 and 100 samples (more than any fixed per-point buffer of 64): on constant fields
+    v_j the loop gives sum_m c_m v_j(m) + alpha*a*b/(1+c^2) with a, b, c the first three
+    samples (all of input 0 here), and leaves the halo alone."""
+    n = 6
+    offs = [(dx, dy) for dy in range(-2, 3) for dx in range(-2, 3)][:per]
+    vals = [0.5 + 0.25 * j for j in range(nin)]
+    dats, args = [DatSpec("o", (n, n), (2, 2), (2, 2))], [Arg("o", WRITE)]
+    for j, v in enumerate(vals):
+        dats.append(DatSpec(f"i{j}", (n, n), (2, 2), (2, 2), init=np.full((n + 4, n + 4), v)))
+        args.append(Arg(f"i{j}", READ, offs))
+    M = nin * per
+    c = [((-1) ** m) / (8.0 * (m + 1)) for m in range(M)]
+    alpha = 0.5
+    fields, _ = _run(oracle_lib, dats, [], [Loop("lincomb", (0, 0), (n, n), args, [alpha] + c)])
+    lin = math.fsum(c[m] * vals[m // per] for m in range(M))
+    v0 = vals[0]
+    expect = lin + alpha * v0 * v0 / (1 + v0 * v0)
+    inner = fields["o"].a[2:-2, 2:-2]
+    assert np.allclose(inner, expect, rtol=1e-14, atol=0)
+    assert np.all(fields["o"].a[:2, :] == 0) and np.all(fields["o"].a[:, -2:] == 0)
+
+
+def test_results_independent_of_thread_count(oracle_lib):
+    """The loop kernels split lines over threads and reductions fold per-row partials in
+    row order, so 1 and 4 threads give the same bits (a 2-D and a 3-D random chain)."""
+    from workloads import random_chain
+    rng = np.random.default_rng(77)
+    cases = [random_chain.build(n=40, nfields=6, nloops=10, seed=5)]
+    dats3, reds3, loops3 = random_chain.build_general(3, 10, 5, 8, 2, seed=9, nz=7)
+    for d in dats3:
+        d.init = rng.uniform(-1, 1, size=d.shape)
+    cases.append((dats3, reds3, loops3))
+    runs = []
+    try:
+        for nthreads in (1, 4):
+            oracle_lib.set_threads(nthreads)
+            out = []
+            for dats, reds, loops in cases:
+                fields, sums = _run(oracle_lib, dats, reds, loops)
+                out.append(({k: v.a.copy() for k, v in fields.items()}, sums))
+            runs.append(out)
+    finally:
+        oracle_lib.set_threads(oracle_lib.threads_default)
+    for (f1, s1), (f4, s4) in zip(*runs):
+        assert s1 == s4
+        for k in f1:
+            assert np.array_equal(f1[k], f4[k]), k
