@@ -78,8 +78,9 @@ static inline bool is_write(int acc) { return acc == OC_WRITE || acc == OC_RW; }
 
 bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
                 const std::vector<int>& red_ops, int h, int depth, uint32_t flags,
-                bool incore, Plan& P, std::string& err)
+                bool incore, Plan& P, std::string& err, const Residency* res)
 {
+    if (incore || (res && !res->any())) res = nullptr;
     P = Plan();
     const int L = (int)loops.size();
     P.L = L;
@@ -181,6 +182,10 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
     // other than x columns), 3 first access a write over x in [wx0, wx1) and the full
     // extent of the other non-slow axes (only the x columns outside it are uploaded)
     std::vector<std::vector<uint8_t>> state(ND), written(ND);
+    // per dataset: 1 if the first loop of the chain that touches it only writes it (a
+    // "write-first" dataset, Sec. 4.1: a per-chain temporary under the cyclic option),
+    // 2 if that loop reads it
+    std::vector<uint8_t> dfirst(ND, 0);
     for (int d = 0; d < ND; ++d) {
         state[d].assign(P.dp[d].nrows, 0);
         written[d].assign(P.dp[d].nrows, 0);
@@ -190,6 +195,12 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
     for (const Loop& lp : loops) {
         int lo = lp.lo[sa], hi = lp.hi[sa];
         if (lo >= hi) continue;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && is_read(ar.access) && !dfirst[P.dat_index[ar.dat]])
+                dfirst[P.dat_index[ar.dat]] = 2;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && is_write(ar.access) && !dfirst[P.dat_index[ar.dat]])
+                dfirst[P.dat_index[ar.dat]] = 1;
         for (const Arg& ar : lp.args)
             if (ar.access != OC_REDUCE && is_read(ar.access)) {
                 int d = P.dat_index[ar.dat];
@@ -227,7 +238,9 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
             if (dp.first[r] < 0) continue;
             const uint8_t st = state[d][r];
             dp.need_up[r] = st == 2 ? 1 : (st == 3 ? 2 : 0);
-            dp.dl[r] = written[d][r] && !(cyclic && (st == 1 || st == 3));
+            // cyclic (Sec. 4.1): a write-first dataset is a per-chain temporary, none of
+            // its rows go back; any other dataset keeps every row it writes
+            dp.dl[r] = written[d][r] && !(cyclic && dfirst[d] == 1);
         }
         // group rows into per-tile intervals (same tile, same copy kind and columns)
         auto group = [&](const std::vector<uint8_t>& need, const std::vector<int>& tile, bool cols,
@@ -248,6 +261,14 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
         };
         group(dp.need_up, dp.first, true, dp.up);
         group(dp.dl, dp.last, false, dp.down);
+        // a resident dataset stays whole in device memory: no copies, no slab
+        if (res && res->off[dp.dat] >= 0) {
+            dp.resident = true;
+            dp.S = dp.nrows;
+            dp.up.clear();
+            dp.down.clear();
+            continue;
+        }
 
         // slab rows: largest span of rows live in one phase. Phase p computes tile p,
         // uploads tile p + k, downloads tile p - 1. A row is live from the phase of its
@@ -320,14 +341,21 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
                 P.loop_chunks[i] = chunks;
                 loop_cnt[i] = plane > 0 ? (long long)std::max(0, loops[i].hi[sa] - loops[i].lo[sa]) * chunks : 0;
             }
-    // ---- arena layout ---------------------------------------------------------------
-    long long off = 0;
+    // ---- arena layout: the resident region first, then the slabs ----------------------
+    long long off = res ? res->bytes : 0;
+    P.res_bytes = off;
     for (int d = 0; d < ND; ++d) {
         DatPlan& dp = P.dp[d];
+        if (dp.resident) {
+            dp.off = res->off[dp.dat];
+            P.res_dats++;
+            continue;
+        }
         dp.off = off;
         off += align_up((long long)dp.S * dats[dp.dat].row_bytes(), 256);
     }
     P.slab_bytes = off;
+    P.res_level = res ? res->level : 0.0;
     off = 0;
     for (size_t r = 0; r < P.rp.size(); ++r) {
         P.rp[r].part_off = off;
@@ -350,6 +378,11 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
     P.arena_bytes = P.slab_bytes + P.scratch_bytes;
     P.sig = chain_signature(loops, dats, flags) ^ ((uint64_t)h * 0x9E3779B1u) ^ ((uint64_t)depth << 56)
             ^ (incore ? 0x5555ull : 0);
+    if (res) {
+        uint64_t r = 0x2545F4914F6CDD1Dull;
+        for (size_t k = 0; k < res->off.size(); ++k) r = mix(r, (uint64_t)(res->off[k] + 1) * 31 + k);
+        P.sig = mix(P.sig, r);
+    }
     P.valid = true;
     (void)err;
     return true;
@@ -357,7 +390,7 @@ bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
 
 int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
                     const std::vector<int>& red_ops, int depth, uint32_t flags,
-                    long long budget, std::string& err)
+                    long long budget, std::string& err, const Residency* res)
 {
     if (loops.empty()) return 1;
     const int sa = loops[0].ndim - 1;
@@ -366,7 +399,7 @@ int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats
     const int span = std::max(1, Y1 - Y0);
     Plan P;
     auto fits = [&](int h) {
-        build_plan(loops, dats, red_ops, h, depth, flags, false, P, err);
+        build_plan(loops, dats, red_ops, h, depth, flags, false, P, err, res);
         return P.arena_bytes <= budget;
     };
     if (!fits(1)) return 0;
@@ -379,6 +412,46 @@ int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats
     // the same number of tiles, evened out: no short last tile (a phase of its own)
     const int T = (span + lo - 1) / lo;
     return (span + T - 1) / T;
+}
+
+Residency choose_residency(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
+                           const std::vector<int>& red_ops, uint32_t flags, long long budget,
+                           double level)
+{
+    Residency R;
+    R.off.assign(dats.size(), -1);
+    R.level = level;
+    if (level <= 0 || loops.empty()) return R;
+    // bytes each dataset moves per chain without residency (tile height: an eighth of
+    // the span, which changes these totals only by the skew of the tile boundaries)
+    const int sa = loops[0].ndim - 1;
+    int Y0 = INT_MAX, Y1 = INT_MIN;
+    for (const Loop& lp : loops) { Y0 = std::min(Y0, lp.lo[sa]); Y1 = std::max(Y1, lp.hi[sa]); }
+    Plan P;
+    std::string err;
+    build_plan(loops, dats, red_ops, std::max(1, (Y1 - Y0) / 8), 3, flags, false, P, err);
+    struct Cand { int dat; double traffic, bytes; };
+    std::vector<Cand> cand;
+    for (const DatPlan& dp : P.dp) {
+        const Dat& d = dats[dp.dat];
+        double rows = 0;
+        for (const Interval& iv : dp.up) if (iv.x0 == iv.x1) rows += iv.b - iv.a;
+        for (const Interval& iv : dp.down) rows += iv.b - iv.a;
+        if (rows > 0) cand.push_back({dp.dat, rows * (double)d.row_bytes(), (double)d.bytes()});
+    }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+        const double ra = a.traffic / a.bytes, rb = b.traffic / b.bytes;
+        if (ra != rb) return ra > rb;
+        return a.traffic > b.traffic;
+    });
+    const long long cap = (long long)(level * (double)budget);
+    for (const Cand& c : cand) {
+        const long long need = align_up((long long)c.bytes, 256);
+        if (R.bytes + need > cap) continue;
+        R.off[c.dat] = R.bytes;
+        R.bytes += need;
+    }
+    return R;
 }
 
 }  // namespace oc

@@ -74,9 +74,10 @@ struct Interval { int t, a, b, x0 = 0, x1 = 0; };
 
 struct DatPlan {
     int dat = -1;
+    bool resident = false;     // kept whole in device memory across chains: no copies
     int S = 0;                 // slab rows; row y lives at slot (y - y0) mod S
     int y0 = 0, nrows = 0;
-    long long off = 0;         // arena byte offset of the slab
+    long long off = 0;         // arena byte offset of the slab (resident: of the dataset)
     std::vector<Interval> up, down;
     std::vector<int> first, last;      // per row: first / last tile touching it, -1 if none
     std::vector<uint8_t> need_up, dl;  // per row: uploaded (1 whole, 2 columns) / downloaded
@@ -88,6 +89,16 @@ struct RedPlan {
     int op = 0;
     long long part_off = 0;   // arena byte offset of this handle's partials
     long long count = 0;      // number of partials (doubles)
+};
+
+// Datasets a streamed plan keeps resident: arena offset per dataset handle (-1 for a
+// streamed dataset), inside a region of `bytes` at the start of the arena, and the share of
+// the budget the region may take (the planner's residency level).
+struct Residency {
+    std::vector<long long> off;
+    long long bytes = 0;
+    double level = 0.0;
+    bool any() const { return bytes > 0; }
 };
 
 struct Plan {
@@ -108,7 +119,10 @@ struct Plan {
     std::vector<int> loop_param;         // per loop: offset (doubles) into the parameter block
     int nparams = 0;
     long long params_off = 0, paramsf_off = 0, results_off = 0;
-    long long slab_bytes = 0;            // bytes of all slabs
+    long long slab_bytes = 0;            // end of the slabs (resident region included)
+    long long res_bytes = 0;             // resident region at the start of the arena
+    int res_dats = 0;                    // datasets kept resident
+    double res_level = 0.0;
     long long scratch_bytes = 0;         // partials + parameters + results
     long long arena_bytes = 0;           // slab_bytes + scratch_bytes
     int s(int t, int i) const { return se[((size_t)t * L + i) * 2]; }
@@ -125,11 +139,17 @@ uint64_t chain_signature(const std::vector<Loop>& loops, const std::vector<Dat>&
                          uint32_t flags);
 bool build_plan(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
                 const std::vector<int>& red_ops, int h, int depth, uint32_t flags,
-                bool incore, Plan& plan, std::string& err);
+                bool incore, Plan& plan, std::string& err, const Residency* res = nullptr);
 // Largest tile height (>= 1) whose plan fits `budget` bytes; 0 if none fits.
 int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
                     const std::vector<int>& red_ops, int depth, uint32_t flags,
-                    long long budget, std::string& err);
+                    long long budget, std::string& err, const Residency* res = nullptr);
+// Residency of a streamed chain at `level` (share of the budget for resident datasets):
+// the datasets the chain moves most bytes for per byte they occupy (uploads plus
+// downloads of one chain, from a plan without residency), taken greedily while they fit.
+Residency choose_residency(const std::vector<Loop>& loops, const std::vector<Dat>& dats,
+                           const std::vector<int>& red_ops, uint32_t flags, long long budget,
+                           double level);
 bool full_row_write(const Loop& lp, const Dat& d);
 
 }  // namespace oc

@@ -249,3 +249,63 @@ def test_planner_features_of_a_chain(lib, nd, dtype):
     assert f[5] == nd
     assert np.log2(fp) - 1e-6 <= f[6] <= np.log2(1.25 * fp)
     assert f[7] == pytest.approx(np.log2(slow), abs=1e-6)
+
+
+def _write_first_datasets(loops):
+    """Datasets whose first loop in the chain only writes them (reads of a loop count
+    before its writes): the per-chain temporaries of the cyclic option (Sec. 4.1)."""
+    first = {}
+    for lp in loops:
+        for a in lp.args:
+            if a.access in ("r", "rw") and a.name not in first:
+                first[a.name] = "r"
+        for a in lp.args:
+            if a.access in ("w", "rw") and a.name not in first:
+                first[a.name] = "w"
+    return {k for k, v in first.items() if v == "w"}
+
+
+def test_cyclic_keeps_datasets_read_before_written(lib, oracle_lib):
+    """Sec. 4.1's cyclic option drops the downloads of datasets written first (per-chain
+    temporaries) -- a property of the dataset, not of its rows. Here `f` is read first on
+    its rows 0..5 and first written on the others: it is not a temporary, so every row it
+    writes goes back, and three chains replayed on tagged slabs equal three oracle chains."""
+    n = 24
+    rng = np.random.default_rng(5)
+    dats = [DatSpec(nm, (n, n), (1, 1), (1, 1), init=rng.uniform(-1, 1, (n + 2, n + 2))) for nm in ("f", "g", "a")]
+    loops = [Loop("copy", (0, 0), (n, 6), [Arg("g", WRITE), Arg("f", READ, [(0, 0)])]),
+             Loop("lincomb", (0, 0), (n, n), [Arg("f", WRITE), Arg("a", READ, [(0, 0), (1, 0)])], [0.0, 0.5, 0.25]),
+             Loop("lincomb", (0, 0), (n, n), [Arg("a", WRITE), Arg("f", READ, [(0, 1), (0, -1)])], [0.0, 0.5, 0.5])]
+    plan, _, names = dry(1 << 30, dats, [], loops, h=5, depth=3, flags=oc.OC_FLAG_CYCLIC)
+    by = {d["dat"]: d for d in plan["dats"]}
+    f = by[names["f"]]
+    down = {y for _, lo, hi, _, _ in f["down"] for y in range(lo, hi)}
+    assert down == set(range(n))
+    assert "g" in _write_first_datasets(loops)
+    assert len(by[names["g"]]["down"]) == 0
+    got, _ = plan_sim.simulate(plan, loops, dats, [], oracle_lib, names, chains=3)
+    ref = oracle_lib.make_fields(dats)
+    for _ in range(3):
+        oracle_lib.run_chain(loops, ref, [])
+    for nm in ("f", "a"):
+        assert np.array_equal(got[nm].a, ref[nm].a), nm
+
+
+@pytest.mark.parametrize("seed,h,depth", [(3, 3, 3), (4, 5, 4)])
+def test_cyclic_random_chains_keep_state(lib, oracle_lib, seed, h, depth):
+    """Random chains with the cyclic option (and the prefetch) replayed for three chains:
+    every dataset that is not write-first carries its state across chains exactly as the
+    oracle does."""
+    dats, reds, loops = random_chain.build(n=30, nfields=8, nloops=16, seed=400 + seed)
+    plan, _, names = dry(1 << 30, dats, reds, loops, h=h, depth=depth,
+                         flags=oc.OC_FLAG_CYCLIC | oc.OC_FLAG_PREFETCH)
+    plan_sim.check_legality(plan, loops)
+    got, _ = plan_sim.simulate(plan, loops, dats, reds, oracle_lib, names, chains=3, prefetch=True)
+    ref = oracle_lib.make_fields(dats)
+    for _ in range(3):
+        oracle_lib.run_chain(loops, ref, reds)
+    temps = _write_first_datasets(loops)
+    kept = [d.name for d in dats if d.name not in temps]
+    assert len(kept) >= 3
+    for nm in kept:
+        assert np.array_equal(got[nm].a, ref[nm].a), nm

@@ -59,10 +59,14 @@ MUTANTS = [
     ("strip_rows_not_uploaded", "dp.need_up[r] = st == 2 ? 1 : (st == 3 ? 2 : 0);",
      "dp.need_up[r] = st == 2 ? 1 : 0;"),
     ("strip_columns_wrong", "dp.wx0[r] = std::max(lp.lo[0], -dd.hlo[0]);", "dp.wx0[r] = std::max(lp.lo[0], 0);"),
-    ("cyclic_skips_read_first_downloads", "dp.dl[r] = written[d][r] && !(cyclic && (st == 1 || st == 3));",
-     "dp.dl[r] = written[d][r] && !(cyclic && st != 0);"),
-    ("read_only_downloaded", "dp.dl[r] = written[d][r] && !(cyclic && (st == 1 || st == 3));",
-     "dp.dl[r] = !(cyclic && (st == 1 || st == 3));"),
+    ("cyclic_skips_read_first_downloads", "dp.dl[r] = written[d][r] && !(cyclic && dfirst[d] == 1);",
+     "dp.dl[r] = written[d][r] && !(cyclic && dfirst[d] != 0);"),
+    ("cyclic_per_row_first_write", "dp.dl[r] = written[d][r] && !(cyclic && dfirst[d] == 1);",
+     "dp.dl[r] = written[d][r] && !(cyclic && (st == 1 || st == 3));"),
+    ("read_only_downloaded", "dp.dl[r] = written[d][r] && !(cyclic && dfirst[d] == 1);",
+     "dp.dl[r] = !(cyclic && dfirst[d] == 1);"),
+    ("first_access_reads_ignored", "if (ar.access != OC_REDUCE && is_read(ar.access) && !dfirst[P.dat_index[ar.dat]])\n                dfirst[P.dat_index[ar.dat]] = 2;",
+     "if (false)\n                dfirst[P.dat_index[ar.dat]] = 2;"),
     ("copy_groups_merge_tiles", "while (r < dp.nrows && need[r] == kind && tile[r] == t && key(r) == kx) ++r;",
      "while (r < dp.nrows && need[r] == kind && key(r) == kx) ++r;"),
     # slab sizes (cyclic slots): rows live in one pipeline phase must fit
