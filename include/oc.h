@@ -272,6 +272,23 @@ typedef struct oc_trace_rec {
 } oc_trace_rec;
 int oc_trace(oc_trace_rec* out, int cap, int* n);
 
+/* Host-side fault injection, for testing error paths without a device fault. Arms a
+ * one-shot failure at `site` (0: a host-to-device row copy, 1: a device-to-host row copy,
+ * 2: a kernel launch of a tile): the next `after` calls at that site proceed, and the one
+ * after them returns OC_ERR_CUDA ("injected fault: ...") from the running call (oc_flush,
+ * oc_reduce, oc_fetch_dat) without calling CUDA. Work queued before it still runs; the
+ * chain is abandoned and the context should be finalized, as after any OC_ERR_CUDA.
+ * after < 0 disarms the site. Errors: OC_ERR_STATE without a context, OC_ERR_ARG on an
+ * unknown site. */
+int oc_inject_fault(int site, long long after);
+
+/* NUMA placement, for reading host-link measurements: *store_node receives the host
+ * NUMA node of the first page of dataset `dat`'s pinned host store (-1 if unknown or not
+ * allocated), *gpu_host_node the host node closest to the current device
+ * (cudaDevAttrHostNumaId; -1 if the system reports none). Errors: OC_ERR_STATE without a
+ * context, OC_ERR_ARG on a bad handle or null pointer. */
+int oc_numa_nodes(int dat, int* store_node, int* gpu_host_node);
+
 /* Message of the last error (static storage, valid until the next call). */
 const char* oc_last_error(void);
 
@@ -339,7 +356,8 @@ int oc_mlp_train(float* params, const float* X, const float* T, int n, int epoch
  *  out       device pointer to one double receiving the result.
  *  stream    cudaStream_t (NULL: the legacy default stream). The call only enqueues
  *            work; synchronise the stream before reading *out.
- * Requires rows * ceil(row_len / 4096) <= 65536, else OC_ERR_ARG. The first call on a
+ * Requires rows * ceil(row_len / 4096) <= 65536 (e.g. 65536 rows of up to 4096 elements,
+ * or 16 rows of 65536), else OC_ERR_ARG. The first call on a
  * device (with that device current) looks up the array's device address; make it
  * before any stream capture. Calls share the array: calls whose work overlaps on the
  * GPU (e.g. on two streams at once) race and must be ordered by the caller. Errors:

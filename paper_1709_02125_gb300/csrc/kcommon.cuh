@@ -13,6 +13,8 @@ namespace dev {
 
 constexpr int kThreadsX = 128;
 constexpr int kRedThreads = 256;
+// points of a slow row per reduction partial (the host's kRedChunk)
+constexpr int kRedPoints = 4096;
 
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -103,6 +105,7 @@ __device__ __forceinline__ double block_fold(double acc, int op)
 
 // Per-row reduction partial: the block (chunk c, row s) folds the points of its chunk
 // of row s with value(x, yl, s) and stores the result at part[(s - row0) * chunks + c].
+// The chunk's points are taken line by line (x fastest), so no point index is divided.
 template <typename F>
 __device__ __forceinline__ void row_partial(const LaunchDesc& d, F value)
 {
@@ -110,13 +113,19 @@ __device__ __forceinline__ void row_partial(const LaunchDesc& d, F value)
     const int s = d.lo[sa] + (int)blockIdx.y;
     const int nxr = d.hi[0] - d.lo[0];
     const long long plane = d.ndim == 3 ? (long long)nxr * (d.hi[1] - d.lo[1]) : (long long)nxr;
-    const long long q0 = (long long)blockIdx.x * 4096;
-    const long long q1 = q0 + 4096 < plane ? q0 + 4096 : plane;
+    const long long q0 = (long long)blockIdx.x * kRedPoints;
+    const long long q1 = q0 + kRedPoints < plane ? q0 + kRedPoints : plane;
     double acc = red_identity(d.red_op);
-    for (long long q = q0 + threadIdx.x; q < q1; q += kRedThreads) {
-        const int x = d.lo[0] + (int)(q % nxr);
-        const int yl = d.ndim == 3 ? d.lo[1] + (int)(q / nxr) : 0;
-        acc = red_apply(d.red_op, acc, value(x, yl, s));
+    if (q1 > q0) {
+        const int l0 = (int)(q0 / nxr), l1 = (int)((q1 - 1) / nxr);
+        for (int l = l0; l <= l1; ++l) {
+            const long long lq = (long long)l * nxr;
+            const int x0 = l == l0 ? (int)(q0 - lq) : 0;
+            const int x1 = l == l1 ? (int)(q1 - lq) : nxr;
+            const int yl = d.ndim == 3 ? d.lo[1] + l : 0;
+            for (int x = x0 + (int)threadIdx.x; x < x1; x += kRedThreads)
+                acc = red_apply(d.red_op, acc, value(d.lo[0] + x, yl, s));
+        }
     }
     acc = block_fold(acc, d.red_op);
     if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;

@@ -340,37 +340,96 @@ __global__ void __launch_bounds__(kThreadsX) k_hilo_add(const __grid_constant__ 
     }
 }
 
-// One block per (chunk of kRedChunk points of a slow row, slow row). The partial of
-// row s, chunk c is stored at part[(s - part_row0) * chunks + c], independent of the
-// tiling, so tiled and untiled runs fold the same partials in the same order.
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; static constexpr int N = 4; };
+template <> struct VecOf<double> { using V = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ double red_mode(double v, int mode)
+{
+    return mode == 1 ? fabs(v) : (mode == 2 ? v * v : v);
+}
+
+// Fold n consecutive elements pa[0..n) (+ pb[0..n) when pb is set) into this thread's
+// accumulator: a scalar head up to the first 16-byte boundary of pa, 16-byte vectors,
+// a scalar tail. Thread k of the block takes head element k, vectors k, k + 256, ...
+// and tail element k (+ 256...), each in that order, so the association is fixed by the
+// segment alone. Both sources go vector only if they share their offset modulo 16.
+template <typename T>
+__device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mode, int op, double& acc)
+{
+    using V = typename VecOf<T>::V;
+    constexpr int N = VecOf<T>::N;
+    const uintptr_t ua = reinterpret_cast<uintptr_t>(pa);
+    const bool vec = (ua % sizeof(T)) == 0 && (!pb || ((reinterpret_cast<uintptr_t>(pb) ^ ua) & 15) == 0);
+    int head = vec ? (int)(((16 - (ua & 15)) & 15) / sizeof(T)) : n;
+    if (head > n) head = n;
+    for (int i = threadIdx.x; i < head; i += kRedThreads) {
+        double v = (double)__ldg(pa + i);
+        if (pb) v = v + (double)__ldg(pb + i);
+        acc = red_apply(op, acc, red_mode(v, mode));
+    }
+    const int nv = (n - head) / N;
+    const V* va = reinterpret_cast<const V*>(pa + head);
+    const V* vb = reinterpret_cast<const V*>(pb ? pb + head : pa);
+    for (int i = threadIdx.x; i < nv; i += kRedThreads) {
+        T ea[N], eb[N];
+        *reinterpret_cast<V*>(ea) = __ldg(va + i);
+        if (pb) *reinterpret_cast<V*>(eb) = __ldg(vb + i);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double v = (double)ea[k];
+            if (pb) v = v + (double)eb[k];
+            acc = red_apply(op, acc, red_mode(v, mode));
+        }
+    }
+    for (int i = head + nv * N + threadIdx.x; i < n; i += kRedThreads) {
+        double v = (double)__ldg(pa + i);
+        if (pb) v = v + (double)__ldg(pb + i);
+        acc = red_apply(op, acc, red_mode(v, mode));
+    }
+}
+
+// One block per (chunk of kRedPoints points of a slow row, group of slow rows): block
+// (c, g) folds chunk c of rows s = lo + g, lo + g + gridDim.y, ... The points of a row
+// are its x-lines in order (one line in 2-D, the y-lines of a z-plane in 3-D), so chunk c
+// covers whole or partial lines; each line segment is contiguous (a REDUCE reads at
+// offset 0 inside the range, which never wraps a periodic axis). The partial of row s,
+// chunk c is stored at part[(s - part_row0) * chunks + c], independent of the tiling, so
+// tiled and untiled runs fold the same partials in the same order.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ LaunchDesc d)
 {
     const int sa = d.ndim - 1;
-    const int s = d.lo[sa] + (int)blockIdx.y;
     const int nxr = d.hi[0] - d.lo[0];
-    const long long plane = d.ndim == 3 ? (long long)nxr * (d.hi[1] - d.lo[1]) : (long long)nxr;
-    const long long q0 = (long long)blockIdx.x * 4096;
-    const long long q1 = q0 + 4096 < plane ? q0 + 4096 : plane;
+    const int nyl = d.ndim == 3 ? d.hi[1] - d.lo[1] : 1;
+    const long long plane = (long long)nxr * nyl;
+    const long long q0 = (long long)blockIdx.x * kRedPoints;
+    const long long q1 = q0 + kRedPoints < plane ? q0 + kRedPoints : plane;
     const int op = d.red_op;
     const int mode = (int)d.params[0];
     const bool two = d.nargs == 3;
     const DView& a = d.v[0];
     const DView& b = d.v[1];
-    const int sla = first_slot(a, s);
-    const int slb = two ? first_slot(b, s) : 0;
-    double acc = red_identity(op);
-    for (long long q = q0 + threadIdx.x; q < q1; q += kRedThreads) {
-        const int x = d.lo[0] + (int)(q % nxr);
-        const int yl = d.ndim == 3 ? d.lo[1] + (int)(q / nxr) : 0;
-        double v = (double)*(col_ptr<T>(a, x, yl) + (long long)sla * a.row_elems);
-        if (two) v = v + (double)*(col_ptr<T>(b, x, yl) + (long long)slb * b.row_elems);
-        if (mode == 1) v = fabs(v);
-        else if (mode == 2) v = v * v;
-        acc = red_apply(op, acc, v);
+    // lines touched by the chunk: one division per block
+    const int l0 = q1 > q0 ? (int)(q0 / nxr) : 0;
+    const int l1 = q1 > q0 ? (int)((q1 - 1) / nxr) : -1;
+    for (int s = d.lo[sa] + (int)blockIdx.y; s < d.hi[sa]; s += (int)gridDim.y) {
+        const long long ra = (long long)first_slot(a, s) * a.row_elems;
+        const long long rb = two ? (long long)first_slot(b, s) * b.row_elems : 0;
+        double acc = red_identity(op);
+        for (int l = l0; l <= l1; ++l) {
+            const long long lq = (long long)l * nxr;
+            const int x0 = l == l0 ? (int)(q0 - lq) : 0;
+            const int x1 = l == l1 ? (int)(q1 - lq) : nxr;
+            const int yl = d.ndim == 3 ? d.lo[1] + l : 0;
+            const T* pa = col_ptr<T>(a, d.lo[0] + x0, yl) + ra;
+            const T* pb = two ? col_ptr<T>(b, d.lo[0] + x0, yl) + rb : nullptr;
+            seg_fold<T>(pa, pb, x1 - x0, mode, op, acc);
+        }
+        acc = block_fold(acc, op);
+        if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
+        __syncthreads();   // block_fold's shared slots are reused by the next row
     }
-    acc = block_fold(acc, op);
-    if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_combine(const double* __restrict__ part, long long n,
@@ -470,7 +529,7 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
         const int sa = d.ndim - 1;
         const int ns = d.hi[sa] - d.lo[sa];
         if (ns <= 0) return cudaSuccess;
-        dim3 grid(d.chunks, ns, 1);
+        dim3 grid(d.chunks, std::min(ns, 65535), 1);
         if (f32) k_reduce<float><<<grid, kRedThreads, 0, st>>>(d);
         else k_reduce<double><<<grid, kRedThreads, 0, st>>>(d);
         return cudaGetLastError();

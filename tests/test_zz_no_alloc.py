@@ -4,9 +4,11 @@ Callers that cannot allocate device memory (inside another component's graph cap
 allocator-free real-time code, a pool that must not grow) get a reduction whose scratch
 lives in a fixed device array inside liboc.so. This test calls it through the C ABI twice
 in a row -- different element types, operators, modes and shapes -- and checks each
-result against an OC_K_REDUCE loop run by the executor on the same values. The two fold
-identical partials in the same order, so they agree to the tolerance the reduction
-tests use (in practice bit for bit). Collected last on purpose.
+result against an OC_K_REDUCE loop run by the executor on the same values. The two run
+the same kernels on the same partial layout and fold them in the same order, so they
+agree bit for bit. The shapes include a region of exactly 65536 one-element rows: the
+largest the fixed scratch takes, and more rows than one launch grid dimension holds.
+Collected last on purpose.
 """
 import ctypes
 
@@ -40,7 +42,7 @@ def test_reduce_noalloc_matches_executor_twice():
     L.oc_reduce_noalloc.restype = ctypes.c_int
     L.oc_noalloc_last_error.restype = ctypes.c_char_p
     rng = np.random.default_rng(2024)
-    cases = [("f64", "sum", 0, 37, 5000), ("f32", "max", 1, 300, 911)]
+    cases = [("f64", "sum", 0, 37, 5000), ("f32", "max", 1, 300, 911), ("f64", "sum", 2, 65536, 1)]
     for dtype, op, mode, ny, nx in cases:
         npdt = np.float64 if dtype == "f64" else np.float32
         data = rng.uniform(-1.0, 1.0, size=(ny + 2, nx + 2)).astype(npdt)
@@ -53,8 +55,7 @@ def test_reduce_noalloc_matches_executor_twice():
         torch.cuda.synchronize()
         assert rc == 0, L.oc_noalloc_last_error()
         got = float(out.item())
-        bound = 1e-12 * float(np.abs(data[1:-1, 1:-1].astype(np.float64)).sum())
-        assert abs(got - expect) <= bound, (dtype, op, got, expect)
+        assert got == expect, (dtype, op, got, expect)
     # a region beyond the fixed scratch is rejected, not truncated
     big = torch.zeros((70000, 1), dtype=torch.float64, device="cuda")
     out = torch.zeros((1,), dtype=torch.float64, device="cuda")
