@@ -32,7 +32,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <sys/syscall.h>
 #include <thread>
+#include <unistd.h>
 #include <unordered_map>
 #include <vector>
 
@@ -131,7 +133,7 @@ struct Ctx {
     std::unordered_map<uint64_t, GraphSet> graphs;
     std::unordered_map<uint64_t, ChainGraph> chain_graphs;
     cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_j1 = nullptr, ev_j2 = nullptr, ev_par = nullptr,
-                ev_res = nullptr;
+                ev_res = nullptr, ev_resup = nullptr;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
     int force_h = 0, force_depth = 0;
     std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
@@ -164,6 +166,9 @@ struct Ctx {
     // index, largest fitting h) of the last autotuned chain
     float features[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<std::array<double, 5>> tune;
+    // host-side fault injection (oc_inject_fault): calls at site k still to pass before
+    // the next one fails; -1 = disarmed
+    long long fault_after[3] = {-1, -1, -1};
     // autotuning trials
     bool trial = false;
     cudaEvent_t tm0 = nullptr, tm1 = nullptr;   // timing events of a trial
@@ -186,6 +191,17 @@ static int wait_event(cudaEvent_t ev, double timeout_s)
         if (el > timeout_s) return fail(OC_ERR_TIMEOUT, "bounded wait expired after %.1f s", el);
         if (el > 1e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+// Injected fault at `site` (0 upload copy, 1 download copy, 2 kernel launch): true when
+// the armed countdown reaches this call, which then fails without calling CUDA.
+static bool injected(int site)
+{
+    long long& n = g->fault_after[site];
+    if (n < 0) return false;
+    if (n > 0) { --n; return false; }
+    n = -1;
+    return true;
 }
 
 static int wait_stream(cudaStream_t s)
@@ -283,6 +299,8 @@ static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cud
                     bytes += (double)w[k] * d.esz * lines;
                 }
         } else {
+            if (injected(up ? 0 : 1))
+                return fail(OC_ERR_CUDA, "injected fault: %s copy of rows [%d, %d)", up ? "upload" : "download", a, a + n);
             if (up) OC_CUDA(cudaMemcpyAsync(dev, host, (size_t)n * rb, cudaMemcpyHostToDevice, s));
             else OC_CUDA(cudaMemcpyAsync(host, dev, (size_t)n * rb, cudaMemcpyDeviceToHost, s));
             bytes += (double)n * rb;
@@ -511,8 +529,16 @@ static int run_tile_two_streams(const std::vector<LaunchDesc>& ds, cudaStream_t 
         if (last[other] >= 0) OC_CUDA(cudaStreamWaitEvent(st2[sk], g->ev_launch[last[other]], 0));
         on[k] = sk;
         used_b = used_b || sk == 1;
-        cudaError_t e = launch_loop(ds[k], st2[sk]);
-        if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", ds[k].kernel, cudaGetErrorString(e));
+        int rc = OC_OK;
+        if (injected(2)) rc = fail(OC_ERR_CUDA, "injected fault: launch of kernel %d", ds[k].kernel);
+        cudaError_t e = rc ? cudaSuccess : launch_loop(ds[k], st2[sk]);
+        if (e != cudaSuccess) rc = fail(OC_ERR_CUDA, "kernel %d launch failed: %s", ds[k].kernel, cudaGetErrorString(e));
+        if (rc) {
+            // join the second stream before giving up (a capture in progress can then end)
+            cudaEventRecord(g->ev_tj, g->s0b);
+            cudaStreamWaitEvent(s, g->ev_tj, 0);
+            return rc;
+        }
         OC_CUDA(cudaEventRecord(g->ev_launch[k], st2[sk]));
     }
     // join: everything after the tile on stream s sees both streams' work
@@ -553,6 +579,7 @@ static int run_tile_kernels(const std::vector<LaunchDesc>& ds, cudaStream_t s,
             OC_CUDA(cudaEventRecordWithFlags(pr.a, s, ext));
         }
         for (size_t j = k; j < k1; ++j) {
+            if (injected(2)) return fail(OC_ERR_CUDA, "injected fault: launch of kernel %d", ds[j].kernel);
             cudaError_t e = launch_loop(ds[j], s);
             if (e != cudaSuccess) return fail(OC_ERR_CUDA, "kernel %d launch failed: %s", ds[j].kernel, cudaGetErrorString(e));
         }
@@ -661,6 +688,65 @@ static void enter_resident_layout()
     }
     g->resident_bytes = off;
     g->resident_mode = true;
+}
+
+// Partial residency (streamed plans that keep some datasets whole in the arena). A
+// dataset resident now but not kept by `keep` at the same offset goes home first: its
+// device copy is downloaded if the host copy is stale, then it is streamed again (or
+// placed anew). keep == nullptr releases every partially resident dataset.
+static int release_residents(const Plan* keep)
+{
+    if (g->resident_mode || g->dryrun) return OC_OK;
+    std::vector<int> drop;
+    for (size_t k = 0; k < g->dats.size(); ++k) {
+        Dat& d = g->dats[k];
+        if (!d.resident) continue;
+        bool kept = false;
+        if (keep && keep->dat_index[k] >= 0) {
+            const DatPlan& dp = keep->dp[keep->dat_index[k]];
+            kept = dp.resident && dp.off == d.res_off;
+        }
+        if (kept) continue;
+        if (d.dev_valid && !d.host_valid)
+            OC_CUDA(cudaMemcpyAsync(d.host, g->arena + d.res_off, (size_t)d.bytes(), cudaMemcpyDeviceToHost, g->st[2]));
+        drop.push_back((int)k);
+    }
+    if (drop.empty()) return OC_OK;
+    int r = wait_stream(g->st[2]);
+    if (r) return r;
+    for (int k : drop) {
+        Dat& d = g->dats[k];
+        d.resident = false;
+        d.dev_valid = false;
+        d.host_valid = true;
+        d.res_off = -1;
+    }
+    return OC_OK;
+}
+
+// Make the datasets plan P keeps resident resident at their offsets (their upload
+// happens with the chain, on the upload stream, while the device copy is not current).
+static int apply_residency(const Plan& P)
+{
+    int r = release_residents(&P);
+    if (r) return r;
+    for (const DatPlan& dp : P.dp) {
+        if (!dp.resident) continue;
+        Dat& d = g->dats[dp.dat];
+        if (!d.resident) {
+            d.resident = true;
+            d.res_off = dp.off;
+            d.dev_valid = false;
+        }
+    }
+    return OC_OK;
+}
+
+static bool residents_pending(const Plan& P)
+{
+    for (const DatPlan& dp : P.dp)
+        if (dp.resident && !g->dats[dp.dat].dev_valid) return true;
+    return false;
 }
 
 // Refresh the halo rows of a periodic slow axis from the opposite end (deep ghosts).
@@ -945,6 +1031,10 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     cudaStream_t s0 = g->st[0], s1 = g->st[1], s2 = g->st[2];
     int rc = ensure_events(std::max(P.T, 1));
     if (rc) return rc;
+    if (!trial && !P.incore) {
+        rc = apply_residency(P);
+        if (rc) return rc;
+    }
 
     // parameters of every loop, one block
     if ((size_t)P.nparams > g->h_params_cap) {
@@ -975,6 +1065,19 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         if (!pf_match) g->pf.active = false;
     }
     if (trial) {
+        // a trial measures the steady state of a plan: its resident datasets go up before
+        // the timing starts (from the host store, which trials never change)
+        bool up = false;
+        for (const DatPlan& dp : P.dp) {
+            if (!dp.resident) continue;
+            const Dat& d = g->dats[dp.dat];
+            OC_CUDA(cudaMemcpyAsync(g->arena + dp.off, d.host, (size_t)d.bytes(), cudaMemcpyHostToDevice, s1));
+            up = true;
+        }
+        if (up) {
+            OC_CUDA(cudaEventRecord(g->ev_resup, s1));
+            OC_CUDA(cudaStreamWaitEvent(s0, g->ev_resup, 0));
+        }
         OC_CUDA(cudaEventRecord(g->tm0, s0));
         OC_CUDA(cudaStreamWaitEvent(s1, g->tm0, 0));
         OC_CUDA(cudaStreamWaitEvent(s2, g->tm0, 0));
@@ -997,7 +1100,7 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     if (P.incore)
         for (const DatPlan& dp : P.dp) incore_uploads = incore_uploads || !g->dats[dp.dat].dev_valid;
     const bool chain_graph = !trial && (g->flags & OC_FLAG_GRAPHS) && !(g->flags & (OC_FLAG_TRACE | OC_FLAG_PROFILE)) &&
-                             !incore_uploads;
+                             !incore_uploads && !(!P.incore && residents_pending(P));
     ChainGraph* cg = nullptr;
     bool replay = false;
     if (chain_graph) {
@@ -1038,13 +1141,12 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     if (!replay) {
         rc = issue_chain(P, loops, trial, chain_graph, pf_match, S, sb, hp, hpf, hr);
         if (chain_graph) {
-            cudaError_t e = cudaSuccess;
-            if (!rc) {
-                e = cudaEventRecord(g->ev_j1, s1);
-                if (e == cudaSuccess) e = cudaEventRecord(g->ev_j2, s2);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j1, 0);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j2, 0);
-            }
+            // the copy streams join the compute stream even after a failure, so that the
+            // capture ends cleanly and no stream is left in capture mode
+            cudaError_t e = cudaEventRecord(g->ev_j1, s1);
+            if (e == cudaSuccess) e = cudaEventRecord(g->ev_j2, s2);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j1, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, g->ev_j2, 0);
             cudaGraph_t gr = nullptr;
             cudaError_t ce = cudaStreamEndCapture(s0, &gr);
             if (rc || e != cudaSuccess || ce != cudaSuccess) {
@@ -1080,8 +1182,14 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         if (!P.incore)
             for (size_t di = 0; di < P.dp.size(); ++di) {
                 const Dat& d = g->dats[P.dp[di].dat];
-                if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+                if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
             }
+        if (P.res_dats > 0)
+            for (const Loop& lp : loops)
+                for (const Arg& ar : lp.args)
+                    if ((ar.access == OC_WRITE || ar.access == OC_RW) && P.dat_index[ar.dat] >= 0 &&
+                        P.dp[P.dat_index[ar.dat]].resident)
+                        g->dats[ar.dat].host_valid = false;
     }
     if (chain_graph) {
         OC_CUDA(cudaGraphLaunch(cg->exec, s0));
@@ -1179,7 +1287,39 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
     } else {
         for (size_t di = 0; di < P.dp.size(); ++di) {
             const Dat& d = g->dats[P.dp[di].dat];
-            if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+            if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+        }
+        // datasets the plan keeps resident: uploaded whole while their device copy is not
+        // current (a trial uploaded them before its timing started), deep ghosts refreshed
+        // on the device
+        if (P.res_dats > 0) {
+            bool up = false;
+            for (const DatPlan& dp : P.dp) {
+                if (!dp.resident) continue;
+                Dat& d = g->dats[dp.dat];
+                if (trial || d.dev_valid) continue;
+                OC_CUDA(cudaMemcpyAsync(g->arena + dp.off, d.host, (size_t)d.bytes(), cudaMemcpyHostToDevice, s1));
+                S.h2d_bytes += (double)d.bytes();
+                d.dev_valid = true;
+                up = true;
+            }
+            if (up) {
+                OC_CUDA(cudaEventRecord(g->ev_resup, s1));
+                OC_CUDA(cudaStreamWaitEvent(s0, g->ev_resup, 0));
+            }
+            for (size_t di = 0; di < P.dp.size(); ++di) {
+                const Dat& d = g->dats[P.dp[di].dat];
+                if (P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
+                    rc = ghost_fill_device(d, s0);
+                    if (rc) return rc;
+                }
+            }
+            if (!trial)
+                for (const Loop& lp : loops)
+                    for (const Arg& ar : lp.args)
+                        if ((ar.access == OC_WRITE || ar.access == OC_RW) && P.dat_index[ar.dat] >= 0 &&
+                            P.dp[P.dat_index[ar.dat]].resident)
+                            g->dats[ar.dat].host_valid = false;
         }
         const int T = P.T, k = P.depth - 2;
         g->up_rec.assign(std::max(T, 1), 0);
@@ -1532,6 +1672,7 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_j2, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_par, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_res, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_resup, cudaEventDisableTiming);
         cudaStreamCreateWithFlags(&c->s0b, cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&c->ev_tf, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_tj, cudaEventDisableTiming);
@@ -1562,7 +1703,8 @@ int oc_finalize(void)
             host_free(kv.second.hp, true);
             host_free(kv.second.hr, true);
         }
-        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res, g->ev_tf, g->ev_tj})
+        for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res, g->ev_resup, g->ev_tf,
+                              g->ev_tj})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : g->ev_launch) cudaEventDestroy(e);
         if (g->s0b) cudaStreamDestroy(g->s0b);
@@ -1766,6 +1908,39 @@ int oc_trace(oc_trace_rec* out, int cap, int* n)
     if (!n || (cap > 0 && !out)) return fail(OC_ERR_ARG, "oc_trace: null");
     *n = (int)g->tr_out.size();
     for (int i = 0; i < cap && i < *n; ++i) out[i] = g->tr_out[i];
+    return OC_OK;
+}
+
+int oc_inject_fault(int site, long long after)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_inject_fault: no context");
+    if (site < 0 || site > 2) return fail(OC_ERR_ARG, "oc_inject_fault: site must be 0, 1 or 2");
+    g->fault_after[site] = after < 0 ? -1 : after;
+    return OC_OK;
+}
+
+int oc_numa_nodes(int dat, int* store_node, int* gpu_host_node)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_numa_nodes: no context");
+    if (dat < 0 || dat >= (int)g->dats.size() || !store_node || !gpu_host_node)
+        return fail(OC_ERR_ARG, "oc_numa_nodes: arguments");
+    *store_node = -1;
+    *gpu_host_node = -1;
+    const Dat& d = g->dats[dat];
+#ifdef SYS_get_mempolicy
+    if (d.host) {
+        int node = -1;
+        // MPOL_F_NODE | MPOL_F_ADDR: the node holding the page at the given address
+        if (syscall(SYS_get_mempolicy, &node, nullptr, 0UL, d.host, 3UL) == 0) *store_node = node;
+    }
+#endif
+    if (!g->dryrun) {
+        int dev = 0, v = -1;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrHostNumaId, dev) == cudaSuccess)
+            *gpu_host_node = v;
+        else
+            cudaGetLastError();
+    }
     return OC_OK;
 }
 

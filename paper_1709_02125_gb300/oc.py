@@ -35,7 +35,7 @@ EXPORTS = ["oc_init", "oc_finalize", "oc_decl_dat", "oc_decl_reduction", "oc_enq
            "oc_reduce", "oc_fetch_dat", "oc_set_flag", "oc_set_tiling", "oc_stats", "oc_last_error",
            "oc_plan_shape", "oc_plan_ranges", "oc_plan_dat", "oc_kernel_stats", "oc_kernel_stats_reset",
            "oc_trace", "oc_planner_features", "oc_autotune_result", "oc_planner_load", "oc_mlp_nparams",
-           "oc_mlp_forward", "oc_mlp_loss_grad", "oc_mlp_train"]
+           "oc_mlp_forward", "oc_mlp_loss_grad", "oc_mlp_train", "oc_numa_nodes", "oc_inject_fault"]
 
 
 class OcArg(ctypes.Structure):
@@ -99,6 +99,8 @@ def load():
     L.oc_kernel_stats.argtypes = [I, ctypes.POINTER(OcKernelStats)]
     L.oc_kernel_stats_reset.argtypes = []
     L.oc_trace.argtypes = [ctypes.POINTER(OcTraceRec), I, IP]
+    L.oc_numa_nodes.argtypes = [I, IP, IP]
+    L.oc_inject_fault.argtypes = [I, ctypes.c_longlong]
     FP = ctypes.POINTER(ctypes.c_float)
     DP = ctypes.POINTER(ctypes.c_double)
     L.oc_planner_features.argtypes = [FP]
@@ -266,6 +268,16 @@ class Executor:
         _check(self.L.oc_trace(arr, n.value, ctypes.byref(n)))
         kinds = ("upload", "compute", "download")
         return [(r.tile, kinds[r.kind], r.start_ms, r.end_ms, r.bytes) for r in arr[:n.value]]
+
+    def inject_fault(self, site: int, after: int):
+        """Arm a one-shot host-side failure (0 upload copy, 1 download copy, 2 launch)."""
+        _check(self.L.oc_inject_fault(int(site), int(after)))
+
+    def numa_nodes(self, name: str) -> tuple:
+        """(host NUMA node of the dataset's pinned store, host node closest to the GPU)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(self.L.oc_numa_nodes(self.names[name], ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def features(self) -> np.ndarray:
         f = np.zeros(8, dtype=np.float32)

@@ -142,3 +142,37 @@ def test_dry_run_plans_but_holds_no_data(dry):
                            ctypes.byref(ndown)) == oc.OC_OK
     rows = sorted(y for j in range(nup.value) for y in range(up[5 * j + 1], up[5 * j + 2]))
     assert rows == list(range(0, 8))   # the interior rows the reduction reads, each once
+
+
+def test_fault_hook_and_numa_query_arguments(L):
+    """oc_inject_fault and oc_numa_nodes: state errors without a context, argument errors
+    on a bad site or handle; a dry-run context arms the hook and plans as before (it
+    issues no copy, so nothing fails) and reports no NUMA node for a store it never
+    allocated."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    assert L.oc_inject_fault(0, 0) == oc.OC_ERR_STATE
+    assert L.oc_numa_nodes(0, ctypes.byref(a), ctypes.byref(b)) == oc.OC_ERR_STATE
+    ptrs = (ctypes.c_void_p * 3)()
+    assert L.oc_init(1 << 20, None, 0, ptrs, oc.OC_FLAG_DRYRUN, oc.OC_PLAN_FIXED) == oc.OC_OK
+    try:
+        assert L.oc_inject_fault(3, 0) == oc.OC_ERR_ARG and "site" in _err(L)
+        assert L.oc_inject_fault(-1, 0) == oc.OC_ERR_ARG
+        for site in (0, 1, 2):
+            assert L.oc_inject_fault(site, 0) == oc.OC_OK
+        assert L.oc_inject_fault(0, -1) == oc.OC_OK   # disarm
+        size = (ctypes.c_int * 3)(64, 64, 1)
+        halo = (ctypes.c_int * 3)(1, 1, 0)
+        h = ctypes.c_int()
+        assert L.oc_decl_dat(2, size, halo, halo, oc.OC_F64, None, 0, ctypes.byref(h)) == oc.OC_OK
+        assert L.oc_numa_nodes(h.value + 1, ctypes.byref(a), ctypes.byref(b)) == oc.OC_ERR_ARG
+        assert L.oc_numa_nodes(h.value, None, ctypes.byref(b)) == oc.OC_ERR_ARG
+        assert L.oc_numa_nodes(h.value, ctypes.byref(a), ctypes.byref(b)) == oc.OC_OK
+        assert a.value == -1 and b.value == -1
+        offs = (ctypes.c_int * 2)(0, 0)
+        args = (oc.OcArg * 2)(oc.OcArg(h.value, oc.OC_WRITE, 1, offs), oc.OcArg(h.value, oc.OC_READ, 1, offs))
+        lo, hi = (ctypes.c_int * 3)(0, 0, 0), (ctypes.c_int * 3)(64, 64, 1)
+        assert L.oc_enqueue_loop(oc.OC_K_COPY, lo, hi, 2, args, None, 0) == oc.OC_OK
+        assert L.oc_inject_fault(2, 0) == oc.OC_OK
+        assert L.oc_flush() == oc.OC_OK
+    finally:
+        assert L.oc_finalize() == oc.OC_OK
