@@ -9,10 +9,12 @@ divided by the step time.
 
 Variants on fresh contexts: the headline mixed+learned form (fields stored and
 computed in FP32, sums in FP64, learned tile planner, prefetch and CUDA graphs), the
-FP64 plain out-of-core form, and FP64 in-core (budget above the footprint).
+FP64 plain out-of-core form, FP64 with the paper's optimisations (prefetch, cyclic) and
+graphs, and FP64 / FP32 in-core (budget above the footprint). Every variant times
+--repeats regions of exactly --steps steps and reports the median region.
 
-`--impl reference` times the oracle (plain untiled FP64 C; its OpenMP loops run over the
-third axis, so on this 2-D workload it uses one host core) on the same workload instead.
+`--impl reference` times the oracle (plain untiled FP64 C; its OpenMP loops split the
+(z, y) lines of every range over the host cores) on the same workload instead.
 """
 from __future__ import annotations
 
@@ -266,10 +268,14 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
 
 
 def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps, warmup, n, dist,
-                profile_kernels=None, spc=1):
+                profile_kernels=None, spc=1, repeats=1, trace=False):
+    """Run one variant on a fresh context: `warmup` untimed steps, then `repeats` timed
+    regions of exactly `steps` steps each (barrier + synchronize around each). The region
+    with the median device time is the variant's figure; all regions are returned."""
     from paper_1709_02125_gb300 import oc
     dats, reds, make_step, fp, ct = build_workload(workload, mixed, n, spc)
     n_datasets = len(dats)
+    first_dat = dats[0].name
     budget = int(fp * budget_frac)
     streams = [torch.cuda.Stream() for _ in range(3)]
     arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
@@ -283,24 +289,31 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
         step = make_step(ex)
         for _ in range(warmup):
             step()
-        s0 = ex.stats()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(streams[1])
-        t0 = time.perf_counter()
-        launches = 0
-        vals = None
-        for _ in range(steps):
-            vals = step()
-            launches += ex.stats()["kernel_launches"]
-        e1.record(streams[2])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        dev_s = e0.elapsed_time(e1) / 1e3
-        dev_s, wall = max_over_ranks(dist, [dev_s, wall], "cuda")
-        s1 = ex.stats()
+        regions = []
+        for _rep in range(repeats):
+            s0 = ex.stats()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(streams[1])
+            t0 = time.perf_counter()
+            launches = 0
+            vals = None
+            for _ in range(steps):
+                vals = step()
+                launches += ex.stats()["kernel_launches"]
+            e1.record(streams[2])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            dev_s = e0.elapsed_time(e1) / 1e3
+            dev_s, wall = max_over_ranks(dist, [dev_s, wall], "cuda")
+            s1 = ex.stats()
+            regions.append({"device_s": dev_s, "wall_s": wall, "launches": launches, "vals": vals,
+                            "s0": s0, "s1": s1})
+        order = sorted(range(len(regions)), key=lambda k: regions[k]["device_s"])
+        med = regions[order[len(order) // 2]]
+        s0, s1 = med["s0"], med["s1"]
         res = {
             "dtype": "f32" if mixed else "f64", "budget_bytes": budget, "footprint_bytes": fp,
             "cells_per_step": (s1["total_cell_updates"] - s0["total_cell_updates"]) / steps,
@@ -308,16 +321,21 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
             "hbm_bytes_per_step": (s1["total_hbm_bytes"] - s0["total_hbm_bytes"]) / steps,
             "h2d_bytes_per_step": (s1["total_h2d_bytes"] - s0["total_h2d_bytes"]) / steps,
             "d2h_bytes_per_step": (s1["total_d2h_bytes"] - s0["total_d2h_bytes"]) / steps,
-            "device_s": dev_s, "wall_s": wall, "tiles": s1["tiles"], "tile_height": s1["tile_height"],
-            "depth": s1["depth"], "kernel_launches": launches, "graph_replays": s1["graph_replays"],
-            "prefetched_bytes": s1["prefetched_bytes"], "sums": vals,
+            "device_s": med["device_s"], "wall_s": med["wall_s"], "tiles": s1["tiles"],
+            "tile_height": s1["tile_height"], "depth": s1["depth"], "kernel_launches": med["launches"],
+            "graph_replays": s1["graph_replays"], "prefetched_bytes": s1["prefetched_bytes"], "sums": med["vals"],
+            "regions_device_s": [r["device_s"] for r in regions], "regions_wall_s": [r["wall_s"] for r in regions],
         }
         res["n_datasets"] = n_datasets
+        try:
+            res["numa"] = dict(zip(("store_node", "gpu_host_node"), ex.numa_nodes(first_dat)))
+        except Exception:  # noqa: BLE001 - diagnostics only
+            res["numa"] = None
         if profile_kernels:
-            # second timed region, same steps, with every launch bracketed by CUDA events on
-            # the compute stream: per-kernel device time, from which the dominant kernel
-            # and its average launch time are taken (kept out of the headline region
-            # because the events add host work between launches)
+            # second pass, same steps, with every run of launches of one kernel bracketed by
+            # CUDA events on the compute stream: per-kernel device time, from which the
+            # dominant kernel and its average launch time are taken (kept out of the timed
+            # regions because the events add host work between launches)
             ex.set_flag(oc.OC_FLAG_PROFILE, True)
             ex.kernel_stats_reset()
             for _ in range(min(steps, 10)):
@@ -326,10 +344,39 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
             res["kstats"] = {k: ex.kernel_stats(k) for k in profile_kernels}
             res["kstats"] = {k: v for k, v in res["kstats"].items() if v["launches"] > 0}
             ex.set_flag(oc.OC_FLAG_PROFILE, False)
+        if trace:
+            # third pass with the per-tile time line (no chain graph, one compute stream):
+            # the rate of every tile's upload and download as the copy engines saw it
+            ex.set_flag(oc.OC_FLAG_TRACE, True)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            res["trace"] = trace_summary(ex.trace())
+            ex.set_flag(oc.OC_FLAG_TRACE, False)
         return res
     finally:
         ex.close()
         del arena
+
+
+def trace_summary(tr):
+    """Per-tile copy rates of one traced chain: median / min / max GB/s of the tile uploads
+    and downloads, the time the upload stream was busy, and the chain's span."""
+    out = {}
+    if not tr:
+        return None
+    end = max(r[3] for r in tr)
+    for kind in ("upload", "download"):
+        rates = [r[4] / (r[3] - r[2]) / 1e6 for r in tr if r[1] == kind and r[4] > 0 and r[3] > r[2]]
+        busy = sum(r[3] - r[2] for r in tr if r[1] == kind and r[4] > 0)
+        if rates:
+            out[kind] = {"tiles": len(rates), "gbs_median": round(float(np.median(rates)), 1),
+                         "gbs_min": round(float(min(rates)), 1), "gbs_max": round(float(max(rates)), 1),
+                         "busy_ms": round(busy, 3)}
+    comp = [r[3] - r[2] for r in tr if r[1] == "compute"]
+    out["compute_ms_per_tile_median"] = round(float(np.median(comp)), 3) if comp else None
+    out["chain_ms"] = round(end, 3)
+    return out
 
 
 def install_learned_planner(torch):
@@ -364,6 +411,7 @@ def reference_main(args):
     import oracle
     from workloads import random_chain
     oracle.build()
+    oracle.set_threads(oracle.threads_default)
     n = args.n
     dats, reds, loops = random_chain.build(n=n)
     fields = oracle.make_fields(dats)
@@ -386,7 +434,7 @@ def reference_main(args):
     cores = oracle_cores_used(sub, oracle.threads())
     sample = f"full chain (42 loops) on {n} x {rows} rows of the {n}^2 grid per step" if rows < n else \
         f"full chain (42 loops) on the full {n}^2 grid per step"
-    sample += f"; {cores} thread(s): the oracle's OpenMP loops run over the third axis"
+    sample += f"; {cores} thread(s): the oracle's OpenMP loops split the y rows over the threads"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -418,31 +466,52 @@ def cpu_model() -> str:
 
 
 def oracle_cores_used(loops, threads: int) -> int:
-    """Threads the oracle actually works with on a chain: its loop kernels split the
-    work over the third axis, so a 2-D chain (one plane) runs on a single thread."""
-    planes = max(((lp.hi[2] - lp.lo[2]) if len(lp.lo) == 3 else 1) for lp in loops)
-    return max(1, min(threads, planes))
+    """Threads the oracle actually works with on a chain: its loop kernels split the (z, y)
+    lines of a range over the threads, so a chain keeps min(threads, lines) of them busy."""
+    lines = 1
+    for lp in loops:
+        n = 1
+        for a in range(1, len(lp.lo)):
+            n *= max(0, lp.hi[a] - lp.lo[a])
+        lines = max(lines, n)
+    return max(1, min(threads, lines))
 
 
-def cpu_baseline(n, budget_s=20.0):
+def _oracle_rate(oracle, loops, fields, reds, budget_s, max_chains=8):
+    """Cell-updates/s of whole chains run back to back for about budget_s seconds."""
+    t0 = time.perf_counter()
+    chains = cells = 0
+    while (time.perf_counter() - t0 < budget_s or chains == 0) and chains < max_chains:
+        oracle.run_chain(loops, fields, reds)
+        chains += 1
+        cells += sum(np.prod([h - l for l, h in zip(lp.lo, lp.hi)]) for lp in loops)
+    dt = time.perf_counter() - t0
+    return float(cells / dt), chains, dt
+
+
+def cpu_baseline(n, budget_s=12.0):
+    """The oracle as it stands, timed on this host at all threads (the reported value) and
+    at one thread on a bounded sample (the first n/8 rows of every loop's range)."""
     import oracle
     from workloads import random_chain
     oracle.build()
     dats, reds, loops = random_chain.build(n=n)
     fields = oracle.make_fields(dats)
-    t0 = time.perf_counter()
-    chains = 0
-    cells = 0
-    while time.perf_counter() - t0 < budget_s and chains < 8:
-        oracle.run_chain(loops, fields, reds)
-        chains += 1
-        cells += sum(np.prod([h - l for l, h in zip(lp.lo, lp.hi)]) for lp in loops)
-    dt = time.perf_counter() - t0
-    threads = oracle.threads()
-    return {"value": float(cells / dt), "unit": UNIT, "cores": oracle_cores_used(loops, threads),
-            "kind": "oracle", "threads_available": threads, "cpu_model": cpu_model(),
-            "sample": f"{chains} full chains (42 loops, {n}^2 grid, FP64) in {dt:.1f} s; the oracle's "
-                      "OpenMP loops run over the third axis, so this 2-D chain uses one thread"}
+    threads = oracle.threads_default
+    oracle.set_threads(threads)
+    v_all, chains, dt = _oracle_rate(oracle, loops, fields, reds, budget_s)
+    rows = max(64, n // 8)
+    sub = [type(lp)(lp.kernel, lp.lo, (lp.hi[0], min(lp.hi[1], rows)), lp.args, lp.params) for lp in loops]
+    oracle.set_threads(1)
+    v_one, chains1, dt1 = _oracle_rate(oracle, sub, fields, reds, budget_s)
+    oracle.set_threads(threads)
+    return {"value": v_all, "unit": UNIT, "cores": oracle_cores_used(loops, threads), "kind": "oracle",
+            "threads_available": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": f"{chains} full chains (42 loops, {n}^2 grid, FP64) in {dt:.1f} s on "
+                      f"{oracle_cores_used(loops, threads)} threads (the oracle's loops split the y rows "
+                      f"over the threads)",
+            "one_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                           "sample": f"{chains1} chains on the first {rows} of {n} rows in {dt1:.1f} s"}}
 
 
 WORKLOADS = {
@@ -496,7 +565,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="grid size (default: the workload's)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_incore,mixed_incore")
+    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_opt,fp64_incore,mixed_incore")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of --steps steps per variant; the median region is reported")
     ap.add_argument("--spc", type=int, default=1, help="tgv / euler: time steps per chain")
     args = ap.parse_args()
     desc, prof_kernels, n_default = WORKLOADS[args.workload]
@@ -543,10 +614,12 @@ def main():
         if name == args.variants.split(",")[0]:
             with Clocks(local) as clk:
                 results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
-                                            args.warmup, args.n, dist, profile_kernels=prof_kernels, spc=args.spc)
+                                            args.warmup, args.n, dist, profile_kernels=prof_kernels, spc=args.spc,
+                                            repeats=args.repeats, trace=True)
         else:
             results[name] = run_variant(torch, args.workload, name, mixed, frac, flags, planner, args.steps,
-                                        args.warmup, args.n, dist, spc=args.spc)
+                                        args.warmup, args.n, dist, spc=args.spc, repeats=args.repeats)
+    link_after = link_bandwidth(torch)
     head_name = args.variants.split(",")[0]
     head = results[head_name]
     N = world
@@ -571,13 +644,19 @@ def main():
                 "share_of_profiled_kernel_time": round(ks["ms"] / total_ms, 4)}
     # binding roofline of the whole pipeline: HBM bytes at peak, link bytes at the link speed
     t_step = head["device_s"] / args.steps
-    t_roof = max(head["hbm_bytes_per_step"] / (hbm_peak * 1e9), head["h2d_bytes_per_step"] / (link["h2d_gbs"] * 1e9),
-                 head["d2h_bytes_per_step"] / (link["d2h_gbs"] * 1e9),
-                 (head["h2d_bytes_per_step"] + head["d2h_bytes_per_step"]) / (link["duplex_gbs"] * 1e9))
+    # the link rates are the better of the probes before and after the timed variants
+    linkb = {k: max(link[k], link_after[k]) for k in link}
+    terms = {"hbm": head["hbm_bytes_per_step"] / (hbm_peak * 1e9),
+             "h2d": head["h2d_bytes_per_step"] / (linkb["h2d_gbs"] * 1e9),
+             "d2h": head["d2h_bytes_per_step"] / (linkb["d2h_gbs"] * 1e9),
+             "duplex": (head["h2d_bytes_per_step"] + head["d2h_bytes_per_step"]) / (linkb["duplex_gbs"] * 1e9)}
+    binding = max(terms, key=terms.get)
+    t_roof = terms[binding]
     variants_out = {}
     for k, r in results.items():
         v = job_throughput(N, r["cells_per_step"], args.steps, r["device_s"])
         variants_out[k] = {"value": v, "dtype": r["dtype"], "ms_per_step": r["device_s"] / args.steps * 1e3,
+                           "ms_per_step_regions": [round(x / args.steps * 1e3, 4) for x in r["regions_device_s"]],
                            "tiles": r["tiles"], "tile_height": r["tile_height"], "depth": r["depth"],
                            "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
                            "budget_bytes": r["budget_bytes"], "footprint_bytes": r["footprint_bytes"]}
@@ -602,7 +681,13 @@ def main():
                    "parallelism": f"replicas x{N}"},
         "roofline": roof,
         "pipeline_roofline": {"t_roof_ms": t_roof * 1e3, "t_ms": t_step * 1e3, "frac": t_roof / t_step,
-                              "link": link, "hbm_peak_gbs": hbm_peak},
+                              "binding": binding, "terms_ms": {k: round(v * 1e3, 4) for k, v in terms.items()},
+                              "link": linkb, "link_before": link, "link_after": link_after, "hbm_peak_gbs": hbm_peak,
+                              "numa": head.get("numa"), "trace": head.get("trace")},
+        "repeats": {"regions": args.repeats, "steps_per_region": args.steps, "reported": "median region",
+                    "value_min": job_throughput(N, head["cells_per_step"], args.steps, max(head["regions_device_s"])),
+                    "value_max": job_throughput(N, head["cells_per_step"], args.steps, min(head["regions_device_s"])),
+                    "ms_per_step_regions": [round(x / args.steps * 1e3, 4) for x in head["regions_device_s"]]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["h2d_bytes_per_step"],
                 "d2h_bytes_per_step": head["d2h_bytes_per_step"] + 8 * max(1, len(head["sums"] or []))},
         "gpu_launches": int(head["kernel_launches"]),

@@ -136,11 +136,13 @@ def test_clover3d_bench_step_structure():
 
 
 def test_cpu_baseline_reports_threads_used_and_model(oracle_lib):
-    """The CPU baseline states the threads the oracle really used (one on a 2-D chain:
-    its OpenMP loops run over the third axis) beside those available, and the CPU model."""
+    """The CPU baseline states the threads the oracle really used (its loops split the y
+    rows of a 2-D chain over the threads) beside those available and the CPU model, and a
+    one-thread figure on a bounded sample."""
     b = bench.cpu_baseline(64, budget_s=0.2)
     assert b["kind"] == "oracle" and b["value"] > 0
-    assert b["cores"] == 1 and b["threads_available"] >= 1
+    assert b["cores"] == min(oracle_lib.threads_default, 64) and b["threads_available"] >= 1
+    assert b["one_thread"]["cores"] == 1 and b["one_thread"]["value"] > 0
     assert isinstance(b["cpu_model"], str) and b["cpu_model"]
 
 
@@ -148,6 +150,7 @@ def test_oracle_cores_used():
     from workloads import random_chain
     _, _, loops2 = random_chain.build_general(2, 16, 4, 4, 1, seed=1)
     _, _, loops3 = random_chain.build_general(3, 8, 4, 4, 1, seed=1, nz=5)
-    assert bench.oracle_cores_used(loops2, 16) == 1
-    assert bench.oracle_cores_used(loops3, 16) == 5
+    assert bench.oracle_cores_used(loops2, 16) == 16    # 16 y rows
+    assert bench.oracle_cores_used(loops2, 64) == 16
+    assert bench.oracle_cores_used(loops3, 64) == 40    # 8 y rows x 5 z planes
     assert bench.oracle_cores_used(loops3, 3) == 3
