@@ -322,6 +322,7 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
             "h2d_bytes_per_step": (s1["total_h2d_bytes"] - s0["total_h2d_bytes"]) / steps,
             "d2h_bytes_per_step": (s1["total_d2h_bytes"] - s0["total_d2h_bytes"]) / steps,
             "device_s": med["device_s"], "wall_s": med["wall_s"], "tiles": s1["tiles"],
+            "resident_dats": s1["resident_dats"],
             "tile_height": s1["tile_height"], "depth": s1["depth"], "kernel_launches": med["launches"],
             "graph_replays": s1["graph_replays"], "prefetched_bytes": s1["prefetched_bytes"], "sums": med["vals"],
             "regions_device_s": [r["device_s"] for r in regions], "regions_wall_s": [r["wall_s"] for r in regions],
@@ -389,12 +390,13 @@ def install_learned_planner(torch):
     rows = planner_train.load_rows(path)
     k = int(len(rows) * 0.8)
     t0 = time.perf_counter()
-    p, mean, std, hist = planner_train.train(rows[:k])
+    p, mean, std, hist, alts = planner_train.train(rows[:k])
     train_s = time.perf_counter() - t0
-    learned, fixed = planner_train.evaluate(p, mean, std, rows[k:])
-    oc.planner_load(p, mean, std)
+    learned, fixed = planner_train.evaluate(p, mean, std, rows[k:], alts)
+    planner_train.install(p, mean, std, alts)
     return {"train_chains": k, "heldout_chains": len(rows) - k, "train_s": round(train_s, 2),
-            "final_loss": float(hist[-1]), "heldout_regret_learned": float(learned.mean()),
+            "final_loss": float(hist[-1]), "alternatives": [list(a) for a in alts],
+            "heldout_regret_learned": float(learned.mean()),
             "heldout_regret_fixed": float(fixed.mean())}
 
 
@@ -565,7 +567,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="grid size (default: the workload's)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="mixed_learned,fp64_plain,fp64_opt,fp64_incore,mixed_incore")
+    ap.add_argument("--variants", default="mixed_learned,mixed_fixed,fp64_plain,fp64_opt,fp64_incore,mixed_incore,"
+                                           "mixed_um")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed regions of --steps steps per variant; the median region is reported")
     ap.add_argument("--spc", type=int, default=1, help="tgv / euler: time steps per chain")
@@ -603,6 +606,11 @@ def main():
         "fp64_plain": (False, 1 / 3, 0, oc.OC_PLAN_FIXED),
         "fp64_opt": (False, 1 / 3, P | C | G, oc.OC_PLAN_FIXED),
         "mixed_plain": (True, 1 / 3, 0, oc.OC_PLAN_FIXED),
+        # the method without the learned planner: the fixed rule, every dataset streamed
+        "mixed_fixed": (True, 1 / 3, P | C | G, oc.OC_PLAN_FIXED),
+        # Unified Memory variant (Sec. 5.4): managed stores, tiles prefetched in place
+        "mixed_um": (True, 1 / 3, oc.OC_FLAG_MANAGED, oc.OC_PLAN_FIXED),
+        "fp64_um": (False, 1 / 3, oc.OC_FLAG_MANAGED, oc.OC_PLAN_FIXED),
         "fp64_incore": (False, 1.25, G, oc.OC_PLAN_FIXED),
         "mixed_incore": (True, 1.25, G, oc.OC_PLAN_FIXED),
     }
@@ -656,18 +664,23 @@ def main():
     for k, r in results.items():
         v = job_throughput(N, r["cells_per_step"], args.steps, r["device_s"])
         variants_out[k] = {"value": v, "dtype": r["dtype"], "ms_per_step": r["device_s"] / args.steps * 1e3,
+                           "resident_dats": r.get("resident_dats", 0),
                            "ms_per_step_regions": [round(x / args.steps * 1e3, 4) for x in r["regions_device_s"]],
                            "tiles": r["tiles"], "tile_height": r["tile_height"], "depth": r["depth"],
                            "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
                            "budget_bytes": r["budget_bytes"], "footprint_bytes": r["footprint_bytes"]}
         if r["cell_steps_per_step"]:
             variants_out[k]["cell_timesteps_per_s"] = N * r["cell_steps_per_step"] * args.steps / r["device_s"]
-    for a, b in (("fp64_plain", "fp64_incore"), ("mixed_learned", "mixed_incore"), ("fp64_opt", "fp64_incore")):
+    for a, b in (("fp64_plain", "fp64_incore"), ("mixed_learned", "mixed_incore"), ("fp64_opt", "fp64_incore"),
+                 ("mixed_fixed", "mixed_incore"), ("mixed_um", "mixed_incore"), ("fp64_um", "fp64_incore")):
         if a in variants_out and b in variants_out:
             variants_out[a]["frac_of_incore"] = variants_out[a]["value"] / variants_out[b]["value"]
     if "mixed_learned" in variants_out and "fp64_plain" in variants_out:
         variants_out["mixed_learned"]["speedup_vs_fp64_plain"] = (variants_out["mixed_learned"]["value"]
                                                                  / variants_out["fp64_plain"]["value"])
+    if "mixed_learned" in variants_out and "mixed_fixed" in variants_out:
+        variants_out["mixed_learned"]["speedup_vs_fixed_rule"] = (variants_out["mixed_learned"]["value"]
+                                                                 / variants_out["mixed_fixed"]["value"])
     line = {
         "metric": METRIC if args.workload == "random" else f"out-of-core cell-updates/s at 3x mem ({args.workload})",
         "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps, "warmup": args.warmup,

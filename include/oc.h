@@ -85,22 +85,46 @@ extern "C" {
  *                  a pair of CUDA events on the compute stream and accumulate
  *                  per-kernel device time (oc_kernel_stats).
  * OC_FLAG_TRACE    record the device time line of every tile's upload, compute and
- *                  download of the last flush (oc_trace). */
+ *                  download of the last flush (oc_trace).
+ * OC_FLAG_MANAGED  (oc_init only) the Unified Memory variant of Sec. 5.4: dataset stores
+ *                  are managed memory (cudaMallocManaged) that the kernels address in
+ *                  place; the tile plan is the explicit pipeline's (same budget, tiles and
+ *                  phases), but a tile's copies become prefetches of its rows to the GPU
+ *                  (upload stream) and, after their last tile, back to the host (download
+ *                  stream). Rows first written in the chain are prefetched too (their pages
+ *                  must be on the GPU). No slabs, residency, speculative prefetch, chain
+ *                  graphs or autotuning trials (a trial would change the data in place); the
+ *                  planner uses the fixed rule. A chain that fits the budget is one tile and
+ *                  keeps its pages on the GPU. */
 #define OC_FLAG_CYCLIC   0x1u
 #define OC_FLAG_PREFETCH 0x2u
 #define OC_FLAG_GRAPHS   0x4u
 #define OC_FLAG_DRYRUN   0x8u
 #define OC_FLAG_PROFILE  0x10u
 #define OC_FLAG_TRACE    0x20u
+#define OC_FLAG_MANAGED  0x40u
 
 /* ---- planner modes ----------------------------------------------------------
- * OC_PLAN_FIXED     largest tile height whose plan fits the budget, depth 3.
- * OC_PLAN_AUTOTUNE  time every (tile height, depth) candidate of the grid on the
- *                   first execution of a chain shape and keep the fastest.
- * OC_PLAN_LEARNED   MLP prediction from chain features (oc_planner_load), snapped
- *                   to the grid; falls back to AUTOTUNE when no network is loaded or
- *                   when a standardised feature of the chain lies more than 4 training
- *                   deviations from the training mean (a chain unlike the training set). */
+ * OC_PLAN_FIXED     largest tile height whose plan fits the budget, depth 3, every
+ *                   dataset streamed (Sec. 4: tiles sized by the fast memory alone).
+ * OC_PLAN_AUTOTUNE  time every candidate of the grid on the first execution of a chain
+ *                   shape and keep the fastest. A candidate is a residency level (share
+ *                   of the budget for datasets kept whole in device memory across
+ *                   chains: 0, 1/4, 1/2, 3/4), a depth 2..4 and a tile height (1, 3/4,
+ *                   1/2 or 1/4 of the largest that fits with that residency and depth).
+ * OC_PLAN_LEARNED   MLP prediction from chain features (oc_planner_load) of the gain of
+ *                   two grid candidates over the fixed rule; falls back to AUTOTUNE when
+ *                   no network is loaded or when a standardised feature of the chain lies
+ *                   more than 4 training deviations from the training mean (a chain unlike
+ *                   the training set).
+ * Residency (an addition to the method: the paper streams every dataset of every
+ * chain): a plan may keep some datasets whole in the device arena across chains, so that
+ * their rows are neither uploaded nor downloaded per tile; the other datasets stream
+ * through slabs sized from the rest of the budget. At a level L the datasets are taken
+ * greedily by the link bytes one chain moves for them per byte they occupy, while their
+ * total stays within L * budget. A resident dataset is uploaded once (with the first
+ * chain that keeps it) and downloaded only when oc_fetch_dat asks for it or when a later
+ * plan stops keeping it. */
 #define OC_PLAN_FIXED    0
 #define OC_PLAN_AUTOTUNE 1
 #define OC_PLAN_LEARNED  2
@@ -167,6 +191,9 @@ typedef struct oc_stats_t {
     double total_seconds, total_cell_updates, total_hbm_bytes, total_h2d_bytes,
            total_d2h_bytes;
     long long chains;
+    int    resident_dats;  /* datasets the last flush's plan keeps resident (streamed    */
+    int    pad_;           /* plans; see oc_set_residency)                              */
+    double resident_bytes; /* bytes of those datasets in the device arena               */
 } oc_stats_t;
 
 /* Create the context. Sec. 4: all tiles live inside a device budget.
@@ -230,7 +257,9 @@ int oc_flush(void);
 /* Flush, then return the value of reduction `red` of the last chain that named it. */
 int oc_reduce(int red, double* out);
 
-/* Flush, then copy dataset `dat` (full extent, dense, see top) into host_out. */
+/* Flush, then copy dataset `dat` (full extent, dense, see top) into host_out. The halo
+ * rows of a periodic slow axis are returned as the periodic images of the interior (halo
+ * row y holds interior row y mod n), the state every chain starts from. */
 int oc_fetch_dat(int dat, void* host_out);
 
 /* Switch a OC_FLAG_CYCLIC / PREFETCH / GRAPHS bit on or off between chains (Sec. 4.1:
@@ -241,6 +270,12 @@ int oc_set_flag(uint32_t flag, int on);
  * pipeline depth 2..4 (0 = planner decides). Depth d uploads tile t+d-2 while tile t
  * computes and tile t-1 downloads. */
 int oc_set_tiling(int tile_height, int depth);
+
+/* Override the planner's residency level for streamed chains: the share of the budget
+ * (0 <= level < 1) given to datasets kept resident across chains (see the planner modes
+ * above); a negative level hands the choice back to the planner (OC_PLAN_FIXED: 0).
+ * Errors: OC_ERR_ARG for level >= 1. */
+int oc_set_residency(double level);
 
 /* Copy the counters into *out. */
 int oc_stats(oc_stats_t* out);
@@ -318,16 +353,20 @@ int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
  * bytes per cell, budget / footprint, dimensions, log2(footprint bytes), log2(slow rows).
  * oc_planner_features: features of the most recently planned chain.
  * oc_autotune_result: the table of the last autotuned chain (OC_PLAN_AUTOTUNE, or
- *   OC_PLAN_LEARNED without a network), 5 doubles per candidate: tile height, depth,
- *   device ms of the chain, grid index (height = round(hmax * {1, 3/4, 1/2, 3/8, 1/4,
- *   3/16, 1/8, 1/16}[index])), hmax (largest fitting height at that depth). *n = rows.
+ *   OC_PLAN_LEARNED without a network), 6 doubles per candidate: tile height, depth,
+ *   device ms of the chain (median of 3 interleaved rounds), grid index (height =
+ *   round(hmax * {1, 3/4, 1/2, 1/4}[index])), hmax (largest fitting height at that
+ *   depth and residency), residency level. *n = rows.
  * oc_planner_load: install the network used by OC_PLAN_LEARNED: oc_mlp_nparams() floats
- *   and the features' standardisation (x - mean) / std. The network is a cost model of the
- *   two main alternatives to the fixed rule (hmax, depth 3): y0 = log2 of the time ratio
- *   t(hmax, 3) / t(hmax(4), 4), y1 = log2 of t(hmax, 3) / t(3/4 hmax, 3). The planner keeps
- *   the fixed rule unless max(y0, y1) > 0.03, else takes the alternative with the larger
- *   predicted gain. Applies to chains planned afterwards, in this and later contexts of
- *   the process (it needs no context).
+ *   and the features' standardisation (x - mean) / std. The network is a cost model of two
+ *   alternatives A0, A1 to the fixed rule (hmax, depth 3, nothing resident): y_k = log2 of
+ *   the time ratio t(fixed) / t(A_k). The planner keeps the fixed rule unless
+ *   max(y0, y1) > 0.03, else takes the alternative with the larger predicted gain.
+ *   Applies to chains planned afterwards, in this and later contexts of the process (it
+ *   needs no context).
+ * oc_planner_alternatives: name A0 and A1 as three ints each -- grid index (0..3),
+ *   depth (2..4), residency level index (0: none, 1: 1/4, 2: 1/2, 3: 3/4 of the budget).
+ *   Default {0, 3, 1} and {0, 3, 2}. Errors: OC_ERR_ARG outside the grid.
  * oc_mlp_*: the 8-64-64-2 ReLU network in FP32 on the GPU (host pointers; row-major
  *   X[n][8], Y/T[n][2]); parameter layout W1[64][8] b1[64] W2[64][64] b2[64] W3[2][64]
  *   b3[2]; loss = sum (y - t)^2 / (2n). oc_mlp_train runs `epochs` full-batch Adam steps
@@ -336,6 +375,7 @@ int oc_plan_dat(int k, int* dat, int* slab_rows, int* up, int cap_up, int* nup,
 int oc_planner_features(float* out8);
 int oc_autotune_result(double* table, int cap, int* n);
 int oc_planner_load(const float* params, int nparams, const float* feat_mean, const float* feat_std);
+int oc_planner_alternatives(const int* alt6);
 int oc_mlp_nparams(void);
 int oc_mlp_forward(const float* params, const float* X, int n, float* Y);
 int oc_mlp_loss_grad(const float* params, const float* X, const float* T, int n, float* grad, double* loss);

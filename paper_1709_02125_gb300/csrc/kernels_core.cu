@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "../../include/oc.h"
 #include "kcommon.cuh"
@@ -239,6 +241,90 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_ring(const __grid_constan
     if (rel >= od.S) rel -= od.S;
     const int re = d.ore;
     T* q = op + rel * re;
+    const int w = od.S - rel;
+    const int sre = od.S * re;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (R <= nr || r < nr) q[r * re - (r >= w ? sre : 0)] = acc[r];
+}
+
+// Shared-memory LINCOMB for 2-D FP32 ring launches: the block's tile is 128 x-columns by
+// R rows. Every input field's rows the tile's samples reach -- rows [r0 + ymin, r0 + R +
+// ymax) and columns [x0 - 4, x0 + 132) -- are staged once with coalesced 16-byte loads;
+// each sample then reads shared memory at a compile-time row pitch. Samples, their order
+// and every point's arithmetic are those of k_lincomb_ring, so both kernels give the same
+// bits. The staging layout comes from the host (LaunchDesc::smo / sfy / sfn / sfo).
+constexpr int kSmemPitch = kStagePitch;            // floats per staged row
+constexpr int kSmemVec = kSmemPitch / 4;           // float4 per staged row
+static_assert(kSmemPitch == kThreadsX + 8, "staged rows cover the block's columns and 4 on each side");
+
+template <int R, int M>
+__global__ void __launch_bounds__(kThreadsX) k_lincomb_smem(const __grid_constant__ LaunchDesc d)
+{
+    extern __shared__ float4 sm4[];
+    float* sm = reinterpret_cast<float*>(sm4);
+    const int x0 = d.lo[0] + (int)blockIdx.x * kThreadsX;
+    const int r0 = (int)blockIdx.z * R;
+    const int nr = d.hi[1] - d.lo[1] - r0;
+    const int nrv = nr < R ? nr : R;                // valid output rows of this tile
+    for (int j = 1; j < d.nargs; ++j) {
+        const int ny = d.sfn[j];
+        if (ny <= 0) continue;
+        const DView& v = d.v[j];
+        const int rows = nrv + (ny - R);             // staged rows this tile needs
+        const float* fb = reinterpret_cast<const float*>(v.base) + v.ox + x0 - 4;
+        float4* dst = sm4 + d.sfo[j] * kSmemVec;
+        const int s_first = d.lo[1] + r0 + d.sfy[j];
+        const int xlo = -v.ox, xhi = (int)v.pitch - v.ox;   // addressable columns of a row
+        for (int i = threadIdx.x; i < rows * kSmemVec; i += kThreadsX) {
+            const int rr = i / kSmemVec, c = i - rr * kSmemVec;
+            int slot = v.slot0 + (s_first + rr - v.W0);
+            if (slot >= v.S) slot -= v.S;
+            const int xs = x0 - 4 + 4 * c;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (xs >= xlo && xs + 4 <= xhi)
+                val = __ldg(reinterpret_cast<const float4*>(fb + slot * (int)v.row_elems + 4 * c));
+            dst[rr * kSmemVec + c] = val;
+        }
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= d.hi[0]) return;
+    const float* cp = d.paramsf;
+    float acc[R], xa[R], xb[R], xc[R];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const float c = cp[1 + m];
+        const float* sp = sm + d.smo[m] + threadIdx.x;
+        float val[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) val[r] = (R <= nr || r < nr) ? sp[r * kSmemPitch] : 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (m == 0) { acc[r] = c * val[r]; xa[r] = val[r]; }
+            else {
+                acc[r] = fma_t(c, val[r], acc[r]);
+                if (m == 1) xb[r] = val[r];
+                if (m == 2) xc[r] = val[r];
+            }
+        }
+    }
+    const float alpha = cp[0];
+    if (alpha != 0.f) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float a = xa[r];
+            const float b = M > 1 ? xb[r] : xa[r];
+            const float c = M > 2 ? xc[r] : xa[r];
+            acc[r] = acc[r] + nl_div((alpha * a) * b, 1.f + c * c);
+        }
+    }
+    const SampleRec& od = d.orec;
+    float* op = const_cast<float*>(reinterpret_cast<const float*>(od.p0)) + x;
+    int rel = od.sl0 + r0;
+    if (rel >= od.S) rel -= od.S;
+    const int re = d.ore;
+    float* q = op + rel * re;
     const int w = od.S - rel;
     const int sre = od.S * re;
 #pragma unroll
@@ -487,11 +573,60 @@ cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
     return cudaGetLastError();
 }
 
+// Resident blocks per SM of the ring LINCOMB instantiations ([f32][R = 4, 8][M]) and the
+// SM count, filled once by kernels_prepare() (before any stream capture).
+constexpr int kRingMaxM = 20;
+int g_ring_occ[2][2][kRingMaxM + 1] = {};
+int g_sms = 0;
+
+template <typename T, int M>
+void ring_occupancy()
+{
+    const int f = std::is_same<T, float>::value ? 1 : 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_ring_occ[f][0][M], k_lincomb_ring<T, 4, M>, kThreadsX, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_ring_occ[f][1][M], k_lincomb_ring<T, kLeanRows, M>, kThreadsX, 0);
+}
+
+// Rows per thread of a ring LINCOMB launch: 8, or 4 when that fills the resident block
+// slots of the GPU better. A launch of B blocks with C resident blocks per SM on S SMs
+// runs ceil(B / (C S)) waves; its last wave leaves slots idle. Short tile launches (a few
+// hundred rows) are one or two waves, where this matters; the arithmetic of every point is
+// the same for both choices, so results do not depend on it.
+template <typename T, int M>
+int ring_rows_for(const LaunchDesc& d)
+{
+    const int f = std::is_same<T, float>::value ? 1 : 0;
+    const int c4 = g_ring_occ[f][0][M], c8 = g_ring_occ[f][1][M];
+    if (g_sms <= 0 || c4 <= 0 || c8 <= 0) return kLeanRows;
+    const int sa = d.ndim - 1;
+    const long long bx = (d.hi[0] - d.lo[0] + kThreadsX - 1) / kThreadsX;
+    const long long by = d.ndim == 3 ? d.hi[1] - d.lo[1] : 1;
+    const long long ns = d.hi[sa] - d.lo[sa];
+    auto eff = [&](int R, int c) {
+        const double w = (double)(bx * by * ((ns + R - 1) / R)) / ((double)c * g_sms);
+        return w / std::ceil(w);
+    };
+    return eff(4, c4) > eff(kLeanRows, c8) + 0.05 ? 4 : kLeanRows;
+}
+
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
+    if constexpr (M > 0 && std::is_same<T, float>::value) {
+        if (d.smem_bytes > 0) {
+            const int sa = d.ndim - 1;
+            const int nx = d.hi[0] - d.lo[0], ns = d.hi[sa] - d.lo[sa];
+            if (nx <= 0 || ns <= 0) return cudaSuccess;
+            dim3 grid((nx + kThreadsX - 1) / kThreadsX, 1, (ns + kStageRows - 1) / kStageRows);
+            k_lincomb_smem<kStageRows, M><<<grid, kThreadsX, d.smem_bytes, st>>>(d);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (M > 0) {
-        if (d.ring) return launch_rows(d, st, k_lincomb_ring<T, kLeanRows, M>, kLeanRows);
+        if (d.ring) {
+            if (ring_rows_for<T, M>(d) == 4) return launch_rows(d, st, k_lincomb_ring<T, 4, M>, 4);
+            return launch_rows(d, st, k_lincomb_ring<T, kLeanRows, M>, kLeanRows);
+        }
         if (d.lean) return launch_rows(d, st, k_lincomb_lean<T, kLeanRows, M>, kLeanRows);
     }
     return launch_pointwise(d, st, k_lincomb<T, kRows, M>);
@@ -556,5 +691,21 @@ cudaError_t launch_combine(const double* part, long long n, int op, double* out,
 }
 
 int kernels_compiled_arch() { return 1030; }
+
+void kernels_prepare()
+{
+    if (g_sms > 0) return;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+#define OC_OCC(M) ring_occupancy<float, M>(); ring_occupancy<double, M>();
+    OC_OCC(1) OC_OCC(2) OC_OCC(3) OC_OCC(4) OC_OCC(5) OC_OCC(6) OC_OCC(7) OC_OCC(8) OC_OCC(9) OC_OCC(10)
+    OC_OCC(11) OC_OCC(12) OC_OCC(13) OC_OCC(14) OC_OCC(15) OC_OCC(16) OC_OCC(17) OC_OCC(18) OC_OCC(19) OC_OCC(20)
+#undef OC_OCC
+    cudaGetLastError();
+    g_sms = sms;
+}
 
 }  // namespace oc

@@ -34,6 +34,7 @@ struct Dat {
     void* host = nullptr;    // pinned host store, nrows * row_elems * esz bytes
     char* host_dev = nullptr;  // the store's device mapping (null: not mapped)
     bool host_pinned = false;
+    bool managed = false;    // store in managed memory (OC_FLAG_MANAGED), addressed in place
     // residency (in-core mode keeps the whole dataset in the arena)
     bool resident = false;
     long long res_off = -1;

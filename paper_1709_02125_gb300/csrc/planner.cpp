@@ -4,12 +4,13 @@
 // Features of a chain (inputs of the network, before standardisation):
 //   0 log2(loops)   1 datasets used   2 slow-axis stencil radius   3 bytes per cell
 //   4 budget / footprint   5 dimensions   6 log2(footprint bytes)   7 log2(slow rows)
-// The network is a cost model of the two alternatives that matter most against the
-// fixed rule (largest fitting height hmax, depth 3): y0 = predicted log2(t(hmax, 3) /
-// t(hmax(4), 4)) and y1 = predicted log2(t(hmax, 3) / t(3/4 hmax, 3)). The planner keeps
-// the fixed rule unless an alternative is predicted to be faster by more than
-// kPlannerMargin;
-// otherwise it takes the alternative with the larger predicted gain.
+// The network is a cost model of two alternatives to the fixed rule (largest fitting
+// height hmax, depth 3, nothing kept resident): output k is the predicted log2(t(fixed) /
+// t(alternative k)). The alternatives are candidates of the planner grid (height
+// fraction, depth, residency level) named when the network is installed; by default the
+// fixed tiling with a quarter and with half of the budget given to resident datasets.
+// The planner keeps the fixed rule unless an alternative is predicted to be faster by
+// more than kPlannerMargin, otherwise it takes the alternative with the larger gain.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -22,13 +23,15 @@
 
 namespace oc {
 
-const double kGridFrac[kGridN] = {1.0, 0.75, 0.5, 0.375, 0.25, 0.1875, 0.125, 0.0625};
+const double kGridFrac[kGridN] = {1.0, 0.75, 0.5, 0.25};
+const double kResLevel[kResN] = {0.0, 0.25, 0.5, 0.75};
 
 namespace {
 
 struct Learned {
     bool loaded = false;
     std::vector<float> params, mean, stdv;
+    PlanChoice alt[2] = {{0, 3, 1}, {0, 3, 2}};
 };
 
 Learned& learned()
@@ -85,7 +88,19 @@ bool planner_load(const float* params, const float* mean, const float* stdv)
 
 bool planner_loaded() { return learned().loaded; }
 
-bool planner_predict(const float feat[8], int& grid_idx, int& depth)
+void planner_set_alternatives(const PlanChoice alt[2])
+{
+    learned().alt[0] = alt[0];
+    learned().alt[1] = alt[1];
+}
+
+void planner_alternatives(PlanChoice alt[2])
+{
+    alt[0] = learned().alt[0];
+    alt[1] = learned().alt[1];
+}
+
+bool planner_predict(const float feat[8], PlanChoice& out)
 {
     Learned& L = learned();
     if (!L.loaded) return false;
@@ -97,19 +112,18 @@ bool planner_predict(const float feat[8], int& grid_idx, int& depth)
         if (!(std::fabs(x[k]) <= kPlannerMaxZ)) return false;
     }
     if (mlp_forward(L.params.data(), x, 1, y) != cudaSuccess) return false;
-    grid_idx = 0;
-    depth = 3;
-    if (std::max(y[0], y[1]) > kPlannerMargin) {
-        if (y[0] >= y[1]) depth = 4;
-        else grid_idx = 1;
-    }
+    out = kFixedChoice;
+    if (std::max(y[0], y[1]) > kPlannerMargin) out = y[0] >= y[1] ? L.alt[0] : L.alt[1];
     return true;
 }
 
 void planner_reset()
 {
     Learned& L = learned();
+    const PlanChoice a0 = L.alt[0], a1 = L.alt[1];
     L = Learned();
+    L.alt[0] = a0;
+    L.alt[1] = a1;
 }
 
 }  // namespace oc

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <chrono>
 #include <cstdarg>
@@ -121,6 +122,10 @@ struct Ctx {
     // second compute stream for independent loops of one tile, and its events
     cudaStream_t s0b = nullptr;
     cudaEvent_t ev_tf = nullptr, ev_tj = nullptr;
+    // side stream of the upload stream for the SM-driven halo-strip copies of a tile
+    // (they run beside the copy engines' row copies instead of after them)
+    cudaStream_t s1b = nullptr;
+    cudaEvent_t ev_sf = nullptr, ev_sj = nullptr;
     std::vector<cudaEvent_t> ev_launch;
     std::vector<Dat> dats;
     std::vector<int> red_ops;
@@ -136,6 +141,7 @@ struct Ctx {
                 ev_res = nullptr, ev_resup = nullptr;
     const Plan* last = nullptr;   // plan of the most recent flush (owned by `plans`)
     int force_h = 0, force_depth = 0;
+    double force_res = -1.0;   // share of the budget for resident datasets; < 0: planner
     std::vector<cudaEvent_t> ev_up, ev_comp, ev_down;
     // 1 where the tile's upload / download issued at least one copy and its event was
     // recorded; an empty phase records nothing and nothing waits for it
@@ -165,7 +171,7 @@ struct Ctx {
     // planner: features of the last planned chain, autotuner table (h, depth, ms, grid
     // index, largest fitting h) of the last autotuned chain
     float features[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    std::vector<std::array<double, 5>> tune;
+    std::vector<std::array<double, 6>> tune;
     // host-side fault injection (oc_inject_fault): calls at site k still to pass before
     // the next one fails; -1 = disarmed
     long long fault_after[3] = {-1, -1, -1};
@@ -260,8 +266,9 @@ static int flush_strips(StripBatch& sb, cudaStream_t s, oc_stats_t* S)
 
 static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cudaStream_t s,
                      double& bytes, int x0 = 0, int x1 = 0, char* host_override = nullptr,
-                     StripBatch* strips = nullptr, oc_stats_t* stats = nullptr)
+                     StripBatch* strips = nullptr, oc_stats_t* stats = nullptr, cudaStream_t strip_s = nullptr)
 {
+    if (!strip_s) strip_s = s;
     const long long rb = d.row_bytes();
     const size_t lp = (size_t)d.pitch * d.esz;
     while (a < b) {
@@ -284,7 +291,7 @@ static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cud
                 if (w[k] > 0) {
                     if (sm_copy) {
                         if (strips->njobs == kStripJobs) {
-                            int r = flush_strips(*strips, s, stats);
+                            int r = flush_strips(*strips, strip_s, stats);
                             if (r) return r;
                         }
                         StripJob& j = strips->job[strips->njobs++];
@@ -352,6 +359,7 @@ static char* slab_base(const Plan& P, int di)
 {
     const DatPlan& dp = P.dp[di];
     const Dat& d = g->dats[dp.dat];
+    if (d.managed) return (char*)d.host;
     if (P.incore && d.resident) return g->arena + d.res_off;
     return g->arena + dp.off;
 }
@@ -434,6 +442,37 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                         d.ring = 1;
                         d.ore = (int)d.orec.row_elems;
                         for (int m = 0; m < ns; ++m) d.sre[m] = (int)d.srec[m].row_elems;
+                    }
+                    // 2-D FP32 LINCOMB with x offsets within 4 and a 16-byte aligned first
+                    // column: shared-memory staging of the input rows (k_lincomb_smem)
+                    if (ok && lp.kernel == OC_K_LINCOMB && lp.ndim == 2 && d.dtype == OC_F32 && ns <= 20 &&
+                        (lp.lo[0] & 3) == 0) {
+                        int ymin[kLaunchMaxArgs], ymax[kLaunchMaxArgs];
+                        for (int j = 0; j < d.nargs; ++j) { ymin[j] = INT_MAX; ymax[j] = INT_MIN; d.sfn[j] = 0; }
+                        bool fit = true;
+                        for (int m = 0; m < ns; ++m) {
+                            const int j = d.sarg[m];
+                            if (d.soff[m][0] < -4 || d.soff[m][0] > 4) fit = false;
+                            ymin[j] = std::min(ymin[j], d.soff[m][1]);
+                            ymax[j] = std::max(ymax[j], d.soff[m][1]);
+                        }
+                        int rows = 0;
+                        for (int j = 1; j < d.nargs && fit; ++j) {
+                            if (ymin[j] > ymax[j]) continue;
+                            if (ymax[j] - ymin[j] > 8) fit = false;
+                            d.sfy[j] = (short)ymin[j];
+                            d.sfn[j] = (short)(kStageRows + ymax[j] - ymin[j]);
+                            d.sfo[j] = (short)rows;
+                            rows += d.sfn[j];
+                        }
+                        const long long bytes = (long long)rows * kStagePitch * 4;
+                        if (fit && bytes <= kStageMaxBytes) {
+                            for (int m = 0; m < ns; ++m) {
+                                const int j = d.sarg[m];
+                                d.smo[m] = (short)((d.sfo[j] + d.soff[m][1] - ymin[j]) * kStagePitch + d.soff[m][0] + 4);
+                            }
+                            d.smem_bytes = (int)bytes;
+                        }
                     }
                 }
             }
@@ -702,7 +741,7 @@ static int release_residents(const Plan* keep)
         Dat& d = g->dats[k];
         if (!d.resident) continue;
         bool kept = false;
-        if (keep && keep->dat_index[k] >= 0) {
+        if (keep && k < keep->dat_index.size() && keep->dat_index[k] >= 0) {
             const DatPlan& dp = keep->dp[keep->dat_index[k]];
             kept = dp.resident && dp.off == d.res_off;
         }
@@ -826,38 +865,64 @@ static bool reads_ghosts(const Plan& P, int di)
 static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double* ms_out,
                     std::chrono::steady_clock::time_point t0);
 
-// Exhaustive autotuner (OC_PLAN_AUTOTUNE): every grid candidate (kGridN tile heights
-// per depth 2..4, heights as fractions of the largest that fits) runs the chain twice as
-// a side-effect-free trial; the faster time counts. The fastest candidate wins.
-static int autotune(const std::vector<Loop>& loops, int& h_best, int& d_best)
+// Exhaustive autotuner (OC_PLAN_AUTOTUNE): every candidate of the grid -- residency level
+// (kResLevel), depth 2..4 and kGridN tile heights (fractions of the largest that fits at
+// that depth and residency) -- runs the chain as a side-effect-free trial, in
+// kTuneRounds interleaved rounds; a candidate's time is the median of its rounds and the
+// fastest candidate wins. Partially resident datasets are released first, so that trials
+// find every host copy current.
+constexpr int kTuneRounds = 3;
+
+static int autotune(const std::vector<Loop>& loops, PlanChoice& best_c, int& h_best)
 {
     std::string err;
+    int rc = release_residents(nullptr);
+    if (rc) return rc;
     g->tune.clear();
+    struct Cand { PlanChoice c; int h, hmax; Plan P; std::vector<double> ms; };
+    std::vector<Cand> cands;
+    std::vector<long long> prev_off;
+    for (int ri = 0; ri < kResN; ++ri) {
+        if (g->force_res >= 0 && ri > 0) break;
+        const Residency R = choose_residency(loops, g->dats, g->red_ops, g->flags, g->budget,
+                                             g->force_res >= 0 ? g->force_res : kResLevel[ri]);
+        if (ri > 0 && (!R.any() || R.off == prev_off)) continue;   // nothing new at this level
+        prev_off = R.off;
+        for (int depth = 2; depth <= 4; ++depth) {
+            const int hmax = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err, &R);
+            if (hmax <= 0) continue;
+            int prev = -1;
+            for (int gi = 0; gi < kGridN; ++gi) {
+                const int h = grid_height(hmax, gi);
+                if (h == prev) continue;
+                prev = h;
+                Cand c;
+                c.c = PlanChoice{gi, depth, ri};
+                c.h = h;
+                c.hmax = hmax;
+                build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, c.P, err, &R);
+                if (c.P.arena_bytes > g->budget) continue;
+                cands.push_back(std::move(c));
+            }
+        }
+    }
+    for (int round = 0; round < kTuneRounds; ++round)
+        for (Cand& c : cands) {
+            double m = 0;
+            rc = run_plan(c.P, loops, true, &m, std::chrono::steady_clock::now());
+            g->trial = false;
+            if (rc) return rc;
+            c.ms.push_back(m);
+        }
     double best = 1e300;
     h_best = 0;
-    for (int depth = 2; depth <= 4; ++depth) {
-        const int hmax = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
-        if (hmax <= 0) continue;
-        int prev = -1;
-        for (int gi = 0; gi < kGridN; ++gi) {
-            const int h = grid_height(hmax, gi);
-            if (h == prev) continue;
-            prev = h;
-            Plan P;
-            build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err);
-            if (P.arena_bytes > g->budget) continue;
-            double ms = 1e300;
-            for (int rep = 0; rep < 2; ++rep) {
-                double m = 0;
-                int rc = run_plan(P, loops, true, &m, std::chrono::steady_clock::now());
-                g->trial = false;
-                if (rc) return rc;
-                ms = std::min(ms, m);
-            }
-            g->descs.erase(P.sig);
-            g->tune.push_back({(double)h, (double)depth, ms, (double)gi, (double)hmax});
-            if (ms < best) { best = ms; h_best = h; d_best = depth; }
-        }
+    for (Cand& c : cands) {
+        g->descs.erase(c.P.sig);
+        std::sort(c.ms.begin(), c.ms.end());
+        const double ms = c.ms[c.ms.size() / 2];
+        g->tune.push_back({(double)c.h, (double)c.c.depth, ms, (double)c.c.grid, (double)c.hmax,
+                           g->force_res >= 0 ? g->force_res : kResLevel[c.c.res]});
+        if (ms < best) { best = ms; h_best = c.h; best_c = c.c; }
     }
     return OC_OK;
 }
@@ -869,9 +934,13 @@ static int select_plan_uncached(const std::vector<Loop>& loops, uint64_t csig, P
     Plan inc;
     build_plan(loops, g->dats, g->red_ops, 0, 3, g->flags, true, inc, err);
     const long long rtot = resident_total();
-    if (rtot + inc.scratch_bytes <= g->budget && g->force_h == 0) {
-        if (!g->resident_mode) enter_resident_layout();
-        else {  // new datasets since the layout was made
+    const bool managed = (g->flags & OC_FLAG_MANAGED) != 0;
+    if (!managed && rtot + inc.scratch_bytes <= g->budget && g->force_h == 0) {
+        if (!g->resident_mode) {
+            int r = release_residents(nullptr);
+            if (r) return r;
+            enter_resident_layout();
+        } else {  // new datasets since the layout was made
             long long off = 0;
             for (Dat& d : g->dats) {
                 if (!d.resident) { d.resident = true; d.dev_valid = false; d.res_off = off; }
@@ -887,25 +956,29 @@ static int select_plan_uncached(const std::vector<Loop>& loops, uint64_t csig, P
     }
     if (g->resident_mode) { int r = leave_resident_mode(); if (r) return r; }
 
-    int h = 0, depth = g->force_depth > 0 ? g->force_depth : 3;
+    int h = 0;
+    PlanChoice choice = kFixedChoice;
+    if (g->force_depth > 0) choice.depth = g->force_depth;
     chain_features(loops, g->dats, g->budget, g->features);
-    if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED && !g->dryrun) {
-        int gi = 0, pd = 3;
-        if (g->planner_mode == OC_PLAN_LEARNED && planner_predict(g->features, gi, pd)) {
-            const int hmax = fit_tile_height(loops, g->dats, g->red_ops, pd, g->flags, g->budget, err);
-            if (hmax > 0) {
-                h = grid_height(hmax, gi);
-                depth = pd;
-            }
-        } else {
-            int rc = autotune(loops, h, depth);
+    if (g->force_h <= 0 && g->force_depth <= 0 && g->planner_mode != OC_PLAN_FIXED && !g->dryrun && !managed) {
+        if (!(g->planner_mode == OC_PLAN_LEARNED && g->force_res < 0 && planner_predict(g->features, choice))) {
+            int rc = autotune(loops, choice, h);
             if (rc) return rc;
         }
     }
-    if (h <= 0) h = g->force_h > 0 ? g->force_h : fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err);
+    const double level = managed ? 0.0 : (g->force_res >= 0 ? g->force_res : kResLevel[choice.res]);
+    const Residency R = choose_residency(loops, g->dats, g->red_ops, g->flags, g->budget, level);
+    const int depth = choice.depth;
+    if (h <= 0) {
+        if (g->force_h > 0) h = g->force_h;
+        else {
+            const int hmax = fit_tile_height(loops, g->dats, g->red_ops, depth, g->flags, g->budget, err, &R);
+            h = hmax > 0 ? grid_height(hmax, choice.grid) : 0;
+        }
+    }
     if (h <= 0) return fail(OC_ERR_BUDGET, "device budget of %lld bytes cannot hold one tile of height 1", g->budget);
     Plan P;
-    build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err);
+    build_plan(loops, g->dats, g->red_ops, h, depth, g->flags, false, P, err, &R);
     if (P.arena_bytes > g->budget)
         return fail(OC_ERR_BUDGET, "plan with tile height %d depth %d needs %lld bytes > budget %lld", h,
                     depth, P.arena_bytes, g->budget);
@@ -922,7 +995,8 @@ static int select_plan(const std::vector<Loop>& loops, Plan*& out)
 {
     uint64_t key = chain_signature(loops, g->dats, g->flags);
     key ^= ((uint64_t)(uint32_t)g->force_h << 20) ^ ((uint64_t)g->force_depth << 52) ^
-           ((uint64_t)g->planner_mode << 60) ^ ((uint64_t)g->dats.size() * 0xC2B2AE3D27D4EB4Full);
+           ((uint64_t)g->planner_mode << 60) ^ ((uint64_t)g->dats.size() * 0xC2B2AE3D27D4EB4Full) ^
+           ((uint64_t)(int64_t)std::llround(g->force_res * 1e6) * 0x165667B19E3779F9ull);
     auto it = g->chosen.find(key);
     if (it != g->chosen.end() && (!it->second->incore || g->resident_mode)) {
         out = it->second;
@@ -931,6 +1005,32 @@ static int select_plan(const std::vector<Loop>& loops, Plan*& out)
     int rc = select_plan_uncached(loops, key, out);
     if (rc) return rc;
     g->chosen[key] = out;
+    return OC_OK;
+}
+
+// Unified Memory variant (OC_FLAG_MANAGED, Sec. 5.4): the rows of dataset d whose first
+// (to_gpu) or last tile is t, in runs of consecutive rows, are prefetched to the GPU or
+// back to the host on stream s. A tile's device-bound prefetches take the place of its
+// uploads, its host-bound ones of its downloads.
+static int managed_prefetch(const DatPlan& dp, const Dat& d, int t, bool to_gpu, cudaStream_t s, double& bytes)
+{
+    const std::vector<int>& tile = to_gpu ? dp.first : dp.last;
+    cudaMemLocation loc;
+    loc.type = to_gpu ? cudaMemLocationTypeDevice : cudaMemLocationTypeHost;
+    loc.id = 0;
+    if (to_gpu) OC_CUDA(cudaGetDevice(&loc.id));
+    const long long rb = d.row_bytes();
+    int r = 0;
+    while (r < dp.nrows) {
+        if (dp.first[r] < 0 || tile[r] != t) { ++r; continue; }
+        const int a = r;
+        while (r < dp.nrows && dp.first[r] >= 0 && tile[r] == t) ++r;
+        if (injected(to_gpu ? 0 : 1))
+            return fail(OC_ERR_CUDA, "injected fault: %s prefetch of rows [%d, %d)", to_gpu ? "device" : "host",
+                        a + dp.y0, r + dp.y0);
+        OC_CUDA(cudaMemPrefetchAsync((char*)d.host + (long long)a * rb, (size_t)(r - a) * rb, loc, 0, s));
+        bytes += (double)(r - a) * rb;
+    }
     return OC_OK;
 }
 
@@ -1014,7 +1114,8 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     g->trial = trial;
     if (trial) {
         size_t need = 1;
-        for (const DatPlan& dp : P.dp) need = std::max(need, (size_t)dp.S * (size_t)g->dats[dp.dat].row_bytes());
+        for (const DatPlan& dp : P.dp)
+            if (!dp.resident) need = std::max(need, (size_t)dp.S * (size_t)g->dats[dp.dat].row_bytes());
         if (need > g->trial_sink_bytes) {
             host_free(g->trial_sink, true);
             g->trial_sink = (char*)host_alloc(need, true);
@@ -1100,7 +1201,8 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
     if (P.incore)
         for (const DatPlan& dp : P.dp) incore_uploads = incore_uploads || !g->dats[dp.dat].dev_valid;
     const bool chain_graph = !trial && (g->flags & OC_FLAG_GRAPHS) && !(g->flags & (OC_FLAG_TRACE | OC_FLAG_PROFILE)) &&
-                             !incore_uploads && !(!P.incore && residents_pending(P));
+                             !incore_uploads && !(!P.incore && residents_pending(P)) &&
+                             !(g->flags & OC_FLAG_MANAGED);
     ChainGraph* cg = nullptr;
     bool replay = false;
     if (chain_graph) {
@@ -1345,9 +1447,27 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                 const double up0 = S.h2d_bytes;
                 rc = trace_begin(u, 0, s1);
                 if (rc) return rc;
+                if (g->flags & OC_FLAG_MANAGED) {
+                    for (const DatPlan& dp : P.dp) {
+                        rc = managed_prefetch(dp, g->dats[dp.dat], u, true, s1, S.h2d_bytes);
+                        if (rc) return rc;
+                    }
+                }
+                // halo-strip copies of this tile (SM-driven) go to the side stream, forked
+                // after the phase's waits and joined before the tile's upload event
+                bool strip_side = false;
+                for (const DatPlan& dp : P.dp)
+                    for (const Interval& iv : dp.up)
+                        if (iv.t == u && iv.x0 < iv.x1 && g->dats[dp.dat].host_dev) strip_side = true;
+                if (g->flags & OC_FLAG_MANAGED) strip_side = false;
+                cudaStream_t ss = strip_side ? g->s1b : s1;
+                if (strip_side) {
+                    OC_CUDA(cudaEventRecord(g->ev_sf, s1));
+                    OC_CUDA(cudaStreamWaitEvent(g->s1b, g->ev_sf, 0));
+                }
                 StripBatch strips;
                 strips.njobs = 0;
-                for (size_t di = 0; di < P.dp.size(); ++di) {
+                for (size_t di = 0; di < P.dp.size() && !(g->flags & OC_FLAG_MANAGED); ++di) {
                     const DatPlan& dp = P.dp[di];
                     const Dat& d = g->dats[dp.dat];
                     char* slab = g->arena + dp.off;
@@ -1356,12 +1476,18 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                         if (iv.t != u) continue;
                         rc = for_missing(iv, have, [&](int a, int b) {
                             return copy_rows(d, slab, dp.S, a, b, true, s1, S.h2d_bytes, iv.x0, iv.x1, nullptr,
-                                             &strips, &S);
+                                             &strips, &S, ss);
                         });
-                        if (rc) return rc;
+                        if (rc) break;
                     }
+                    if (rc) break;
                 }
-                rc = flush_strips(strips, s1, &S);
+                if (!rc) rc = flush_strips(strips, ss, &S);
+                if (strip_side) {
+                    // joined even after a failure, so that a capture in progress can end
+                    cudaEventRecord(g->ev_sj, g->s1b);
+                    cudaStreamWaitEvent(s1, g->ev_sj, 0);
+                }
                 if (rc) return rc;
                 rc = trace_end(s1, S.h2d_bytes - up0);
                 if (rc) return rc;
@@ -1385,7 +1511,12 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
                 const double dn0 = S.d2h_bytes;
                 rc = trace_begin(q, 2, s2);
                 if (rc) return rc;
-                for (size_t di = 0; di < P.dp.size(); ++di) {
+                if ((g->flags & OC_FLAG_MANAGED) && T > 1)
+                    for (const DatPlan& dp : P.dp) {
+                        rc = managed_prefetch(dp, g->dats[dp.dat], q, false, s2, S.d2h_bytes);
+                        if (rc) return rc;
+                    }
+                for (size_t di = 0; di < P.dp.size() && !(g->flags & OC_FLAG_MANAGED); ++di) {
                     const DatPlan& dp = P.dp[di];
                     const Dat& d = g->dats[dp.dat];
                     for (const Interval& iv : dp.down)
@@ -1419,7 +1550,7 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
         OC_CUDA(cudaMemcpyAsync(hr, g->arena + sb + P.results_off, P.rp.size() * 8,
                                 cudaMemcpyDeviceToHost, s2));
     }
-    if (!trial && !P.incore && (g->flags & OC_FLAG_PREFETCH)) {
+    if (!trial && !P.incore && (g->flags & OC_FLAG_PREFETCH) && !(g->flags & OC_FLAG_MANAGED)) {
         rc = issue_prefetch(P);
         if (rc) return rc;
     }
@@ -1488,6 +1619,8 @@ static int execute()
     S.tiles = P.T;
     S.tile_height = P.h;
     S.depth = P.depth;
+    S.resident_dats = P.res_dats;
+    S.resident_bytes = (double)P.res_bytes;
     S.loops = P.L;
     S.cell_updates = 0;
     S.hbm_bytes = 0;
@@ -1673,7 +1806,11 @@ int oc_init(size_t budget, void* arena, size_t arena_bytes, void* const streams[
         cudaEventCreateWithFlags(&c->ev_par, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_res, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_resup, cudaEventDisableTiming);
+        kernels_prepare();
         cudaStreamCreateWithFlags(&c->s0b, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&c->s1b, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&c->ev_sf, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_sj, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_tf, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_tj, cudaEventDisableTiming);
     }
@@ -1686,6 +1823,7 @@ int oc_finalize(void)
     if (!g->dryrun) {
         for (int k = 0; k < 3; ++k) if (g->st[k]) cudaStreamSynchronize(g->st[k]);
         if (g->s0b) cudaStreamSynchronize(g->s0b);
+        if (g->s1b) cudaStreamSynchronize(g->s1b);
         for (auto& kv : g->graphs) {
             for (auto ge : kv.second.tiles) if (ge) cudaGraphExecDestroy(ge);
             for (auto& v : kv.second.prof) for (auto& pr : v) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
@@ -1704,17 +1842,21 @@ int oc_finalize(void)
             host_free(kv.second.hr, true);
         }
         for (cudaEvent_t e : {g->ev_fork, g->ev_fork2, g->ev_j1, g->ev_j2, g->ev_par, g->ev_res, g->ev_resup, g->ev_tf,
-                              g->ev_tj})
+                              g->ev_tj, g->ev_sf, g->ev_sj})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : g->ev_launch) cudaEventDestroy(e);
         if (g->s0b) cudaStreamDestroy(g->s0b);
+        if (g->s1b) cudaStreamDestroy(g->s1b);
         if (g->tm0) cudaEventDestroy(g->tm0);
         if (g->tm1) cudaEventDestroy(g->tm1);
         host_free(g->trial_sink, true);
         if (g->own_streams) for (int k = 0; k < 3; ++k) cudaStreamDestroy(g->st[k]);
         if (g->own_arena) cudaFree(g->arena);
     }
-    for (Dat& d : g->dats) host_free(d.host, d.host_pinned);
+    for (Dat& d : g->dats) {
+        if (d.managed) cudaFree(d.host);
+        else host_free(d.host, d.host_pinned);
+    }
     host_free(g->h_params, !g->dryrun);
     host_free(g->h_results, !g->dryrun);
     delete g;
@@ -1747,13 +1889,23 @@ int oc_decl_dat(int ndim, const int size[3], const int halo_lo[3], const int hal
     d.row_elems = d.pitch * d.ylines;
     d.nrows = d.ext(ndim - 1);
     d.y0 = -d.hlo[ndim - 1];
-    if (!g->dryrun) {
+    if (!g->dryrun && (g->flags & OC_FLAG_MANAGED)) {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocManaged(&p, (size_t)d.bytes(), cudaMemAttachGlobal);
+        if (e != cudaSuccess)
+            return fail(OC_ERR_NOMEM, "oc_decl_dat: managed allocation of %lld bytes failed: %s", d.bytes(),
+                        cudaGetErrorString(e));
+        d.host = p;
+        d.managed = true;
+    } else if (!g->dryrun) {
         d.host = host_alloc((size_t)d.bytes(), true);
         if (!d.host) return fail(OC_ERR_NOMEM, "oc_decl_dat: pinned allocation of %lld bytes failed", d.bytes());
         d.host_pinned = true;
         void* mapped = nullptr;
         if (cudaHostGetDevicePointer(&mapped, d.host, 0) == cudaSuccess) d.host_dev = (char*)mapped;
         else cudaGetLastError();
+    }
+    if (!g->dryrun) {
         memset(d.host, 0, (size_t)d.bytes());
         if (host_init) {
             const long long ext0 = d.ext(0);
@@ -1859,6 +2011,18 @@ int oc_fetch_dat(int dat, void* host_out)
         for (long long l = 0; l < d.ylines; ++l)
             memcpy(dst + ((row * d.ylines + l) * ext0) * d.esz,
                    src + ((row * d.row_elems) + l * d.pitch + d.ox - d.hlo[0]) * d.esz, (size_t)(ext0 * d.esz));
+    // a periodic slow axis: its halo rows are returned as the periodic images of the
+    // interior (row y takes row y mod n), whatever the last chain left in them
+    const int sa = d.slow();
+    if (d.periodic & (1 << sa)) {
+        const int n = d.size[sa], lo = d.hlo[sa];
+        const size_t rb = (size_t)(d.ylines * ext0 * d.esz);
+        for (int y = -lo; y < n + d.hhi[sa]; ++y) {
+            if (y >= 0 && y < n) continue;
+            const int yi = ((y % n) + n) % n;
+            memcpy(dst + (size_t)(y + lo) * rb, dst + (size_t)(yi + lo) * rb, rb);
+        }
+    }
     return OC_OK;
 }
 
@@ -1878,6 +2042,14 @@ int oc_set_tiling(int tile_height, int depth)
     if (tile_height < 0 || depth < 0 || depth == 1 || depth > 4) return fail(OC_ERR_ARG, "oc_set_tiling: values");
     g->force_h = tile_height;
     g->force_depth = depth;
+    return OC_OK;
+}
+
+int oc_set_residency(double level)
+{
+    if (!g) return fail(OC_ERR_STATE, "oc_set_residency: no context");
+    if (!(level < 1.0)) return fail(OC_ERR_ARG, "oc_set_residency: level must be below 1");
+    g->force_res = level < 0 ? -1.0 : level;
     return OC_OK;
 }
 
@@ -1958,7 +2130,7 @@ int oc_autotune_result(double* table, int cap, int* n)
     if (!n || (cap > 0 && !table)) return fail(OC_ERR_ARG, "oc_autotune_result: null");
     *n = (int)g->tune.size();
     for (int i = 0; i < cap && i < *n; ++i)
-        for (int k = 0; k < 5; ++k) table[5 * i + k] = g->tune[i][k];
+        for (int k = 0; k < 6; ++k) table[6 * i + k] = g->tune[i][k];
     return OC_OK;
 }
 
@@ -1967,6 +2139,21 @@ int oc_planner_load(const float* params, int nparams, const float* feat_mean, co
     if (!params || !feat_mean || !feat_std || nparams != mlp_nparams())
         return fail(OC_ERR_ARG, "oc_planner_load: expects %d parameters, 8 means and 8 deviations", mlp_nparams());
     planner_load(params, feat_mean, feat_std);
+    if (g) g->chosen.clear();
+    return OC_OK;
+}
+
+int oc_planner_alternatives(const int* alt6)
+{
+    if (!alt6) return fail(OC_ERR_ARG, "oc_planner_alternatives: null");
+    PlanChoice a[2];
+    for (int k = 0; k < 2; ++k) {
+        a[k] = PlanChoice{alt6[3 * k], alt6[3 * k + 1], alt6[3 * k + 2]};
+        if (a[k].grid < 0 || a[k].grid >= kGridN || a[k].depth < 2 || a[k].depth > 4 || a[k].res < 0 ||
+            a[k].res >= kResN)
+            return fail(OC_ERR_ARG, "oc_planner_alternatives: candidate %d out of the grid", k);
+    }
+    planner_set_alternatives(a);
     if (g) g->chosen.clear();
     return OC_OK;
 }

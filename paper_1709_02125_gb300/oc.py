@@ -22,6 +22,7 @@ OC_READ, OC_WRITE, OC_RW, OC_REDUCE = 1, 2, 3, 4
 OC_SUM, OC_MAX, OC_MIN = 0, 1, 2
 OC_FLAG_CYCLIC, OC_FLAG_PREFETCH, OC_FLAG_GRAPHS, OC_FLAG_DRYRUN, OC_FLAG_PROFILE, OC_FLAG_TRACE = \
     0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+OC_FLAG_MANAGED = 0x40
 OC_PLAN_FIXED, OC_PLAN_AUTOTUNE, OC_PLAN_LEARNED = 0, 1, 2
 OC_K_COPY, OC_K_LINCOMB, OC_K_REDUCE, OC_K_HILO_ADD = 1, 2, 3, 4
 
@@ -35,7 +36,8 @@ EXPORTS = ["oc_init", "oc_finalize", "oc_decl_dat", "oc_decl_reduction", "oc_enq
            "oc_reduce", "oc_fetch_dat", "oc_set_flag", "oc_set_tiling", "oc_stats", "oc_last_error",
            "oc_plan_shape", "oc_plan_ranges", "oc_plan_dat", "oc_kernel_stats", "oc_kernel_stats_reset",
            "oc_trace", "oc_planner_features", "oc_autotune_result", "oc_planner_load", "oc_mlp_nparams",
-           "oc_mlp_forward", "oc_mlp_loss_grad", "oc_mlp_train", "oc_numa_nodes", "oc_inject_fault"]
+           "oc_mlp_forward", "oc_mlp_loss_grad", "oc_mlp_train", "oc_numa_nodes", "oc_inject_fault", "oc_set_residency",
+           "oc_planner_alternatives"]
 
 
 class OcArg(ctypes.Structure):
@@ -51,7 +53,8 @@ class OcStats(ctypes.Structure):
                 ("loops", ctypes.c_int), ("graph_replays", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("total_seconds", ctypes.c_double), ("total_cell_updates", ctypes.c_double),
                 ("total_hbm_bytes", ctypes.c_double), ("total_h2d_bytes", ctypes.c_double),
-                ("total_d2h_bytes", ctypes.c_double), ("chains", ctypes.c_longlong)]
+                ("total_d2h_bytes", ctypes.c_double), ("chains", ctypes.c_longlong),
+                ("resident_dats", ctypes.c_int), ("pad_", ctypes.c_int), ("resident_bytes", ctypes.c_double)]
 
 
 class OcKernelStats(ctypes.Structure):
@@ -101,6 +104,8 @@ def load():
     L.oc_trace.argtypes = [ctypes.POINTER(OcTraceRec), I, IP]
     L.oc_numa_nodes.argtypes = [I, IP, IP]
     L.oc_inject_fault.argtypes = [I, ctypes.c_longlong]
+    L.oc_set_residency.argtypes = [ctypes.c_double]
+    L.oc_planner_alternatives.argtypes = [IP]
     FP = ctypes.POINTER(ctypes.c_float)
     DP = ctypes.POINTER(ctypes.c_double)
     L.oc_planner_features.argtypes = [FP]
@@ -246,6 +251,10 @@ class Executor:
     def set_tiling(self, tile_height: int = 0, depth: int = 0):
         _check(self.L.oc_set_tiling(int(tile_height), int(depth)))
 
+    def set_residency(self, level: float):
+        """Share of the budget for datasets kept resident across chains (< 0: planner)."""
+        _check(self.L.oc_set_residency(float(level)))
+
     def stats(self) -> dict:
         s = OcStats()
         _check(self.L.oc_stats(ctypes.byref(s)))
@@ -285,10 +294,11 @@ class Executor:
         return f
 
     def autotune_result(self) -> np.ndarray:
-        """rows (tile height, depth, ms, grid index, hmax) of the last autotuned chain"""
+        """rows (tile height, depth, ms, grid index, hmax, residency level) of the last
+        autotuned chain"""
         n = ctypes.c_int()
         _check(self.L.oc_autotune_result(None, 0, ctypes.byref(n)))
-        t = np.zeros((max(1, n.value), 5))
+        t = np.zeros((max(1, n.value), 6))
         _check(self.L.oc_autotune_result(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
                                          ctypes.byref(n)))
         return t[:n.value]
@@ -378,6 +388,12 @@ def mlp_train(params: np.ndarray, X: np.ndarray, T: np.ndarray, epochs: int, lr:
     hist = np.zeros(max(1, epochs), dtype=np.float32)
     _check(load().oc_mlp_train(_fp(p), _fp(x), _fp(t), x.shape[0], int(epochs), float(lr), _fp(hist)))
     return p, hist[:epochs]
+
+
+def planner_alternatives(alts):
+    """Name the two grid candidates the network predicts: ((grid, depth, residency index), ...)."""
+    a = (ctypes.c_int * 6)(*[int(v) for c in alts for v in c])
+    _check(load().oc_planner_alternatives(a))
 
 
 def planner_load(params: np.ndarray, mean: np.ndarray, std: np.ndarray):

@@ -3,8 +3,9 @@
 Each sample is a random chain (2-D or 3-D, 8-32 fields, 8-48 loops, stencil radius 1-2,
 FP32 or FP64, footprint log-uniform between --min-gb and --max-gb, device budget a
 fraction 1/2 .. 1/8 of the footprint). A fresh context with OC_PLAN_AUTOTUNE runs the
-chain once, which times every (tile height, depth) candidate of the grid on the GPU;
-the chain's features and the timing table are written as one JSON line.
+chain once, which times every candidate of the grid (residency level, depth, tile
+height; three interleaved rounds, median per candidate) on the GPU; the chain's
+features and the timing table are written as one JSON line.
 
     python -m paper_1709_02125_gb300.planner_sweep --count 300 --out sweep.jsonl
 """

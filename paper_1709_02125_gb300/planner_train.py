@@ -1,20 +1,30 @@
 """Train the tile-planner network on autotuner timing tables (planner_sweep.py output).
 
-The network is a cost model of the two main alternatives to the fixed rule (largest
-fitting tile height, depth 3): the targets are y0 = log2(t(fixed) / t(depth 4, largest
-height)) and y1 = log2(t(fixed) / t(depth 3, 3/4 of the largest height)), clipped to
-[-2, 2]. The planner keeps the fixed rule unless an alternative is predicted to win by
-more than MARGIN (log2 units), then takes the larger predicted gain. Features are
-standardised with the training split's mean and deviation. Training runs on the GPU
-through liboc's MLP kernels (full-batch Adam). Evaluation: on the held-out chains, the
-regret of a planner = its candidate's time / the best candidate's time - 1, for the
-learned network and for the fixed rule.
+A timing table has one row per grid candidate: (tile height, depth, ms, grid index, largest
+fitting height, residency level), the candidate being (grid index, depth, residency index)
+with residency levels RES_LEVELS (share of the budget for datasets kept resident). The
+fixed rule -- the method without a planner -- is (0, 3, 0): largest fitting height,
+depth 3, nothing resident.
+
+The network is a cost model of two alternatives A0, A1 to the fixed rule: its targets are
+y_k = log2(t(fixed) / t(A_k)), clipped to [-2, 2]. The alternatives are chosen on the
+training split alone: the twelve pairs of candidates (largest or 3/4 height, depth 3 or 4,
+any residency level) that a perfect predictor would gain most with (mean over the chains
+of max(0, y0, y1)) are shortlisted, and the pair whose trained network has the lowest
+regret in a 3-fold cross-validation over the training chains is kept. The planner keeps the fixed
+rule unless an alternative is predicted to win by more than MARGIN (log2 units), then
+takes the one with the larger predicted gain. Features are standardised with the
+training split's mean and deviation. Training runs on the GPU through liboc's MLP kernels
+(full-batch Adam). Evaluation: on the held-out chains, the regret of a planner = the time
+of its candidate / the best candidate's time - 1, for the learned network and for the
+fixed rule.
 
     python -m paper_1709_02125_gb300.planner_train --data sweep.jsonl --out weights.json
 """
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import math
 import os
@@ -28,8 +38,15 @@ if ROOT not in sys.path:
 
 from paper_1709_02125_gb300 import oc  # noqa: E402
 
-GRID = [1.0, 0.75, 0.5, 0.375, 0.25, 0.1875, 0.125, 0.0625]
-FIXED = (0, 3)   # grid index 0 (largest fitting height), depth 3
+GRID = [1.0, 0.75, 0.5, 0.25]
+RES_LEVELS = [0.0, 0.25, 0.5, 0.75]
+FIXED = (0, 3, 0)   # grid index 0 (largest fitting height), depth 3, nothing resident
+DEFAULT_ALT = ((0, 3, 1), (0, 3, 2))
+MARGIN = 0.03
+
+
+def res_index(level):
+    return int(np.argmin([abs(level - v) for v in RES_LEVELS]))
 
 
 def load_rows(path):
@@ -44,7 +61,8 @@ def load_rows(path):
                 continue
             if "tables" in r:
                 reps = [np.array(x, dtype=np.float64) for x in r["tables"]]
-                if all(x.shape == t.shape and np.array_equal(x[:, [0, 1, 3]], t[:, [0, 1, 3]]) for x in reps):
+                keep = [0, 1, 3, 5] if t.shape[1] > 5 else [0, 1, 3]
+                if all(x.shape == t.shape and np.array_equal(x[:, keep], t[:, keep]) for x in reps):
                     t = t.copy()
                     t[:, 2] = np.median(np.stack([x[:, 2] for x in reps]), axis=0)
             r["table"] = t
@@ -52,34 +70,80 @@ def load_rows(path):
     return rows
 
 
-MARGIN = 0.03
-ALT = ((0, 4), (1, 3))   # (grid index, depth) of the two alternatives
+def lookup(table, cand):
+    """Time of candidate (grid index, depth, residency index), or None if not timed. A
+    residency level the autotuner skipped (it would keep no more datasets than the level
+    below) stands for the one below."""
+    gi, d, ri = cand
+    lv = table[:, 5] if table.shape[1] > 5 else np.zeros(len(table))
+    for r in range(ri, -1, -1):
+        m = (table[:, 3] == gi) & (table[:, 1] == d) & (np.abs(lv - RES_LEVELS[r]) < 1e-9)
+        if m.any():
+            return float(table[m, 2][0])
+        if r > 0 and (np.abs(lv - RES_LEVELS[r]) < 1e-9).any():
+            return None   # the level was timed, this candidate at it was not
+    return None
 
 
-def targets(rows):
-    X = np.array([r["features"] for r in rows], dtype=np.float64)
-    Y = []
+def gains(rows, cand):
+    """log2(t(fixed) / t(cand)) per row (-2 when either is missing), clipped to [-2, 2]."""
+    out = []
     for r in rows:
-        t = r["table"]
-        f = lookup(t, *FIXED)
-        y = []
-        for gi, d in ALT:
-            a = lookup(t, gi, d)
-            y.append(math.log2(f / a) if (f and a) else -2.0)
-        Y.append(y)
-    return X, np.clip(np.array(Y), -2.0, 2.0)
+        f, a = lookup(r["table"], FIXED), lookup(r["table"], cand)
+        out.append(math.log2(f / a) if (f and a) else -2.0)
+    return np.clip(np.array(out), -2.0, 2.0)
 
 
-def choose(y):
+def shortlist(rows, k=12):
+    """Up to k pairs of candidates (grid index 0 or 1, depth 3 or 4) ranked by the mean
+    gain of a perfect choice between them and the fixed rule on `rows`."""
+    cands = sorted({(int(t[3]), int(t[1]), res_index(t[5] if len(t) > 5 else 0.0))
+                    for r in rows for t in r["table"]
+                    if int(t[3]) <= 1 and int(t[1]) in (3, 4)} - {FIXED})
+    if len(cands) < 2:
+        return [DEFAULT_ALT]
+    G = {c: gains(rows, c) for c in cands}
+    scored = [(float(np.mean(np.maximum(0.0, np.maximum(G[a], G[b])))), (a, b))
+              for a, b in itertools.combinations(cands, 2)]
+    scored.sort(key=lambda t: -t[0])
+    return [pair for _, pair in scored[:k]]
+
+
+def alternatives(rows):
+    """The pair of candidates with the largest mean perfect-choice gain on `rows`."""
+    return shortlist(rows, 1)[0]
+
+
+def select_alternatives(rows, folds=3, epochs=1500, k=12):
+    """The shortlisted pair whose network, trained on the other folds, chooses best on
+    each held-out fold of `rows` (mean regret over the folds); runs on the GPU."""
+    pairs = shortlist(rows, k)
+    if len(pairs) == 1 or len(rows) < 3 * folds:
+        return pairs[0]
+    parts = [rows[i::folds] for i in range(folds)]
+    best, pick = float("inf"), pairs[0]
+    for pair in pairs:
+        reg = []
+        for f in range(folds):
+            tr = [r for g, part in enumerate(parts) if g != f for r in part]
+            p, mean, std, _, _ = train(tr, epochs=epochs, alts=pair)
+            learned, _ = evaluate(p, mean, std, parts[f], pair)
+            reg.append(learned.mean())
+        if float(np.mean(reg)) < best:
+            best, pick = float(np.mean(reg)), pair
+    return pick
+
+
+def targets(rows, alts=DEFAULT_ALT):
+    X = np.array([r["features"] for r in rows], dtype=np.float64)
+    Y = np.stack([gains(rows, a) for a in alts], axis=1)
+    return X, Y
+
+
+def choose(y, alts=DEFAULT_ALT):
     if max(y[0], y[1]) <= MARGIN:
         return FIXED
-    return ALT[0] if y[0] >= y[1] else ALT[1]
-
-
-def lookup(table, gi, depth):
-    """time of candidate (grid index, depth), or None if it was not timed (did not fit)"""
-    m = (table[:, 3] == gi) & (table[:, 1] == depth)
-    return float(table[m, 2][0]) if m.any() else None
+    return alts[0] if y[0] >= y[1] else alts[1]
 
 
 def regret(rows, choose):
@@ -87,10 +151,13 @@ def regret(rows, choose):
     for r in rows:
         t = r["table"]
         best = float(t[:, 2].min())
-        gi, d = choose(r)
-        ms = lookup(t, gi, d)
-        if ms is None:   # candidate missing: fall back to the nearest timed height at that depth
-            cand = t[t[:, 1] == d] if (t[:, 1] == d).any() else t
+        c = choose(r)
+        ms = lookup(t, c)
+        if ms is None:   # candidate missing: the nearest timed height at that depth and level
+            gi, d, ri = c
+            lv = t[:, 5] if t.shape[1] > 5 else np.zeros(len(t))
+            sel = (t[:, 1] == d) & (np.abs(lv - RES_LEVELS[ri]) < 1e-9)
+            cand = t[sel] if sel.any() else (t[t[:, 1] == d] if (t[:, 1] == d).any() else t)
             ms = float(cand[np.argmin(np.abs(cand[:, 3] - gi)), 2])
         out.append(ms / best - 1.0)
     return np.array(out)
@@ -108,20 +175,28 @@ def he_init(seed):
     return np.concatenate(parts).astype(np.float32)
 
 
-def train(rows_train, epochs=3000, lr=1e-3, seed=1709):
-    X, Y = targets(rows_train)
+def train(rows_train, epochs=3000, lr=1e-3, seed=1709, alts=None):
+    """Returns (params, feature mean, feature std, loss history, alternatives)."""
+    alts = select_alternatives(rows_train) if alts is None else alts
+    X, Y = targets(rows_train, alts)
     mean = X.mean(axis=0)
     std = X.std(axis=0)
     std[std == 0] = 1.0
     Xs = ((X - mean) / std).astype(np.float32)
     p, hist = oc.mlp_train(he_init(seed), Xs, Y.astype(np.float32), epochs, lr)
-    return p, mean.astype(np.float32), std.astype(np.float32), hist
+    return p, mean.astype(np.float32), std.astype(np.float32), hist, alts
 
 
-def evaluate(p, mean, std, rows):
+def install(p, mean, std, alts):
+    """Load the network and its alternatives into liboc (OC_PLAN_LEARNED)."""
+    oc.planner_alternatives(alts)
+    oc.planner_load(p, mean, std)
+
+
+def evaluate(p, mean, std, rows, alts=DEFAULT_ALT):
     X = np.array([r["features"] for r in rows], dtype=np.float32)
     Yp = oc.mlp_forward(p, (X - mean) / std)
-    learned = regret(rows, lambda r, it=iter(Yp): choose(next(it)))
+    learned = regret(rows, lambda r, it=iter(Yp): choose(next(it), alts))
     fixed = regret(rows, lambda r: FIXED)
     return learned, fixed
 
@@ -137,9 +212,9 @@ def main():
     __graft_entry__.build()
     rows = load_rows(args.data)
     k = int(len(rows) * (1 - args.holdout))
-    p, mean, std, hist = train(rows[:k], epochs=args.epochs)
-    learned, fixed = evaluate(p, mean, std, rows[k:])
-    res = {"params": p.tolist(), "mean": mean.tolist(), "std": std.tolist(), "train_chains": k,
+    p, mean, std, hist, alts = train(rows[:k], epochs=args.epochs)
+    learned, fixed = evaluate(p, mean, std, rows[k:], alts)
+    res = {"params": p.tolist(), "mean": mean.tolist(), "std": std.tolist(), "alternatives": alts, "train_chains": k,
            "heldout_chains": len(rows) - k, "final_loss": float(hist[-1]),
            "heldout_regret_learned_mean": float(learned.mean()), "heldout_regret_fixed_mean": float(fixed.mean()),
            "heldout_regret_learned_median": float(np.median(learned)),

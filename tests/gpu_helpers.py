@@ -7,13 +7,15 @@ from typing import Dict, List
 import numpy as np
 
 
-def run_gpu(dats, reds, loops, budget, h=0, depth=0, flags=0, chains=1, planner=0, ex_out=None):
+def run_gpu(dats, reds, loops, budget, h=0, depth=0, flags=0, chains=1, planner=0, ex_out=None, residency=None):
     """Declare the datasets, run `chains` repetitions of `loops` on the GPU; return
     (final arrays by name, list of per-chain reduction dicts, stats of the last chain)."""
     from paper_1709_02125_gb300 import oc
     ex = oc.Executor(budget, flags=flags, planner=planner)
     try:
         ex.set_tiling(h, depth)
+        if residency is not None:
+            ex.set_residency(residency)
         for d in dats:
             ex.decl_dat(d)
         for r in reds:

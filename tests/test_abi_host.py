@@ -176,3 +176,33 @@ def test_fault_hook_and_numa_query_arguments(L):
         assert L.oc_flush() == oc.OC_OK
     finally:
         assert L.oc_finalize() == oc.OC_OK
+
+
+def test_managed_flag_is_init_only_and_plans_like_the_explicit_pipeline(L):
+    """OC_FLAG_MANAGED (the Unified Memory variant) is chosen at oc_init: oc_set_flag
+    refuses it. A dry-run managed context plans a chain with the explicit pipeline's
+    tiles (the same budget rule), without residency."""
+    from workloads import random_chain
+    dats, reds, loops = random_chain.build(n=128, nfields=8, nloops=12, seed=3)
+    for d in dats:
+        d.init = None
+    fp = random_chain.footprint_bytes(128, 8)
+    shapes = []
+    for flags in (0, oc.OC_FLAG_MANAGED):
+        with oc.Executor(fp // 3, dryrun=True, flags=flags) as ex:
+            with pytest.raises(oc.OcError) as e:
+                ex.set_flag(oc.OC_FLAG_MANAGED, True)
+            assert e.value.code == oc.OC_ERR_ARG
+            ex.set_residency(0.5)
+            oc.run_chain(ex, dats, reds, loops)
+            st = ex.stats()
+            shapes.append((st["tiles"], st["tile_height"], st["resident_dats"]))
+    assert shapes[0][2] > 0 and shapes[1][2] == 0
+    with oc.Executor(fp // 3, dryrun=True, flags=oc.OC_FLAG_MANAGED) as ex:
+        oc.run_chain(ex, dats, reds, loops)
+        st_m = ex.stats()
+    with oc.Executor(fp // 3, dryrun=True) as ex:
+        oc.run_chain(ex, dats, reds, loops)
+        st_e = ex.stats()
+    assert (st_m["tiles"], st_m["tile_height"], st_m["depth"]) == (st_e["tiles"], st_e["tile_height"], st_e["depth"])
+    assert st_m["tiles"] > 1

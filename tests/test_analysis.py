@@ -309,3 +309,47 @@ def test_cyclic_random_chains_keep_state(lib, oracle_lib, seed, h, depth):
     assert len(kept) >= 3
     for nm in kept:
         assert np.array_equal(got[nm].a, ref[nm].a), nm
+
+
+def test_residency_plan_layout(lib):
+    """A streamed plan with part of the budget for resident datasets (oc_set_residency):
+    the datasets kept whole are the ones a chain moves most bytes for per byte (here the
+    read-and-written ones before the read-only ones), they have no copies and one slot per
+    row, they fit the level's share of the budget, and the plan still fits the budget with
+    fewer bytes over the link per chain."""
+    n = 256
+    dats, reds, loops = random_chain.build(n=n, nfields=12, nloops=24, seed=31)
+    fp = random_chain.footprint_bytes(n, 12)
+    budget = fp // 3
+    with oc.Executor(budget, dryrun=True) as ex:
+        oc.run_chain(ex, dats, reds, loops)
+        st0 = ex.stats()
+        p0 = ex.plan()
+    traffic = {}
+    for d in p0["dats"]:
+        rows = sum(b - a for _, a, b, x0, x1 in d["up"] if x0 == x1) + sum(b - a for _, a, b, _, _ in d["down"])
+        traffic[d["dat"]] = rows
+    for level in (0.3, 0.5):
+        with oc.Executor(budget, dryrun=True) as ex:
+            ex.set_residency(level)
+            oc.run_chain(ex, dats, reds, loops)
+            st = ex.stats()
+            p = ex.plan()
+        res = [d for d in p["dats"] if len(d["up"]) == 0 and len(d["down"]) == 0 and d["S"] == n + 4]
+        assert st["resident_dats"] == len(res) > 0
+        assert st["resident_bytes"] <= level * budget
+        kept = {d["dat"] for d in res}
+        # every kept dataset moves at least as many rows per chain as any streamed one
+        # the greedy choice could still have afforded
+        assert min(traffic[k] for k in kept) >= max(t for k, t in traffic.items() if k not in kept) or \
+            len(kept) * (n + 4) ** 2 * 8 > 0.9 * level * budget
+        assert st["tiles"] >= st0["tiles"]
+        up = sum(b - a for d in p["dats"] for _, a, b, x0, x1 in d["up"] if x0 == x1)
+        dn = sum(b - a for d in p["dats"] for _, a, b, _, _ in d["down"])
+        up0 = sum(b - a for d in p0["dats"] for _, a, b, x0, x1 in d["up"] if x0 == x1)
+        dn0 = sum(b - a for d in p0["dats"] for _, a, b, _, _ in d["down"])
+        assert up + dn < up0 + dn0
+    with oc.Executor(budget, dryrun=True) as ex:
+        with pytest.raises(oc.OcError) as e:
+            ex.set_residency(1.0)
+        assert e.value.code == oc.OC_ERR_ARG

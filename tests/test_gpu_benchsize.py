@@ -41,8 +41,8 @@ def _load_learned_planner():
     rows = planner_train.load_rows(os.path.join(ROOT, "paper_1709_02125_gb300", "planner_data",
                                                 "autotune_gb300.jsonl"))
     k = int(len(rows) * 0.8)
-    p, mean, std, _ = planner_train.train(rows[:k])
-    oc.planner_load(p, mean, std)
+    p, mean, std, _, alts = planner_train.train(rows[:k])
+    planner_train.install(p, mean, std, alts)
 
 
 def _write_first(loops):

@@ -87,33 +87,43 @@ def test_autotune_trials_have_no_side_effects():
         oc.run_chain(ex, dats, reds, loops)
         table = ex.autotune_result()
         st = ex.stats()
-    assert len(table) >= 12 and set(table[:, 1]) == {2.0, 3.0, 4.0}
+    # residency levels 0, 1/4, 1/2, 3/4 (those that keep datasets) x depths 2..4 x heights
+    assert len(table) >= 24 and set(table[:, 1]) == {2.0, 3.0, 4.0}
+    assert {0.0, 0.5} <= set(table[:, 5])
     best = table[np.argmin(table[:, 2])]
     assert st["tile_height"] == int(best[0]) and st["depth"] == int(best[1])
+    assert (st["resident_dats"] > 0) == (best[5] > 0)
 
 
-@pytest.mark.parametrize("bias,expect", [((0.5, 0.1), (0, 4)), ((0.0, 0.4), (1, 3)), ((-1.0, 0.02), (0, 3))])
-def test_learned_planner_decision(bias, expect):
-    """A network whose outputs are its biases: y0 / y1 are the predicted log2 gains of
-    (hmax at depth 4) and (3/4 hmax at depth 3) over the fixed rule (hmax, depth 3)."""
+@pytest.mark.parametrize("bias,alts,expect", [
+    ((0.5, 0.1), ((0, 4, 0), (1, 3, 0)), (0, 4, 0)),
+    ((0.0, 0.4), ((0, 4, 0), (1, 3, 0)), (1, 3, 0)),
+    ((-1.0, 0.02), ((0, 4, 0), (1, 3, 0)), (0, 3, 0)),
+    ((0.3, 0.6), ((0, 3, 1), (0, 3, 2)), (0, 3, 2))])
+def test_learned_planner_decision(bias, alts, expect):
+    """A network whose outputs are its biases: y0 / y1 are the predicted log2 gains of the
+    two named alternatives (grid index, depth, residency index) over the fixed rule."""
     from oracle import mlp
     from paper_1709_02125_gb300 import oc
     dats, reds, loops, fp = _chain()
     p = np.zeros(mlp.NPARAMS, dtype=np.float32)
     p[-2:] = bias
     # a wide standardisation keeps every feature of the test chain in distribution
+    oc.planner_alternatives(alts)
     oc.planner_load(p, np.zeros(8), np.full(8, 1e6))
     _, _, st_l = run_gpu(dats, reds, loops, fp // 3, planner=oc.OC_PLAN_LEARNED)
-    gi, depth = expect
-    _, _, st_f = run_gpu(dats, reds, loops, fp // 3, depth=depth)
+    gi, depth, ri = expect
+    _, _, st_f = run_gpu(dats, reds, loops, fp // 3, depth=depth, residency=(0.0, 0.25, 0.5, 0.75)[ri])
     hmax = st_f["tile_height"]
     assert st_l["depth"] == depth
     assert st_l["tile_height"] == max(1, math.floor(hmax * (1.0, 0.75)[gi] + 0.5))
+    assert st_l["resident_dats"] == st_f["resident_dats"] and (st_l["resident_dats"] > 0) == (ri > 0)
 
 
-def test_learned_planner_regret_on_heldout_chains():
+def test_learned_planner_beats_fixed_rule_on_heldout_chains():
     """Train on the committed autotuner sweep (first 80 % of the chains) with the GPU
-    kernels; report the held-out regret of the learned planner and of the fixed rule."""
+    kernels; on the held-out chains the learned planner's mean regret (time of its choice
+    over the best candidate's, minus one) is below the fixed rule's."""
     import os
     from paper_1709_02125_gb300 import planner_train
     path = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_1709_02125_gb300", "planner_data",
@@ -121,15 +131,13 @@ def test_learned_planner_regret_on_heldout_chains():
     rows = planner_train.load_rows(path)
     assert len(rows) >= 100
     k = int(len(rows) * 0.8)
-    p, mean, std, hist = planner_train.train(rows[:k])
+    p, mean, std, hist, alts = planner_train.train(rows[:k])
     assert hist[-1] < hist[0]
-    learned, fixed = planner_train.evaluate(p, mean, std, rows[k:])
+    learned, fixed = planner_train.evaluate(p, mean, std, rows[k:], alts)
     print(f"held-out regret: learned {learned.mean():.4f}, fixed rule {fixed.mean():.4f} "
-          f"({len(rows) - k} chains)")
+          f"({len(rows) - k} chains; alternatives {alts})")
     assert np.all(np.isfinite(learned)) and np.all(learned >= 0)
-    # the learned planner never picks a candidate outside its three options, so its worst
-    # case is bounded by the worse of them
-    assert learned.mean() <= 3 * fixed.mean() + 0.05
+    assert learned.mean() < fixed.mean()
 
 
 def test_learned_planner_abstains_out_of_distribution():
@@ -139,12 +147,12 @@ def test_learned_planner_abstains_out_of_distribution():
     from paper_1709_02125_gb300 import oc
     dats, reds, loops, fp = _chain()
     p = np.zeros(mlp.NPARAMS, dtype=np.float32)
-    p[-2:] = (0.5, 0.1)                      # would choose depth 4 if it answered
+    p[-2:] = (0.5, 0.1)                      # would choose an alternative if it answered
     oc.planner_load(p, np.zeros(8), np.full(8, 1e-3))
     with oc.Executor(fp // 3, planner=oc.OC_PLAN_LEARNED) as ex:
         oc.run_chain(ex, dats, reds, loops)
         table = ex.autotune_result()
         st = ex.stats()
-    assert len(table) >= 12
+    assert len(table) >= 24
     best = table[np.argmin(table[:, 2])]
     assert st["tile_height"] == int(best[0]) and st["depth"] == int(best[1])
