@@ -539,10 +539,11 @@ def kernel_symbol(name: str, dtype: str) -> str:
     return f"k_lincomb_ring<{t}>" if name == "lincomb" else f"k_{name}<{t}>"
 
 
-def recorded_traffic(workload: str, variant: str):
+def recorded_traffic(workload: str, variant: str, plan=None):
     """DRAM bytes per launch of the dominant kernel from a committed ncu capture
     (profiles/traffic.json), or None when the kernel's source text (between the
-    recorded markers) changed since."""
+    recorded markers) changed since, or when the run's plan (tile height, datasets kept
+    resident) differs from the captured one, since a launch's bytes follow its rows."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -554,6 +555,10 @@ def recorded_traffic(workload: str, variant: str):
     a, b = text.find(rec["from"]), text.find(rec["to"])
     if a < 0 or b < a or hashlib.sha256(text[a:b].encode()).hexdigest() != rec["source_sha256"]:
         return None
+    if plan is not None:
+        for k in ("tile_height", "resident_dats"):
+            if k in rec and k in plan and rec[k] != plan[k]:
+                return None
     return rec
 
 
@@ -641,7 +646,7 @@ def main():
         ks = kall[top]
         total_ms = sum(v["ms"] for v in kall.values())
         achieved = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
-        tr = recorded_traffic(args.workload, head_name)
+        tr = recorded_traffic(args.workload, head_name, head)
         roof = {"bound": "hbm", "kernel": kernel_symbol(top, head["dtype"]),
                 "achieved": round(achieved, 1), "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4),

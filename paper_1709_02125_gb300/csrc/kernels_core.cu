@@ -248,90 +248,6 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_ring(const __grid_constan
         if (R <= nr || r < nr) q[r * re - (r >= w ? sre : 0)] = acc[r];
 }
 
-// Shared-memory LINCOMB for 2-D FP32 ring launches: the block's tile is 128 x-columns by
-// R rows. Every input field's rows the tile's samples reach -- rows [r0 + ymin, r0 + R +
-// ymax) and columns [x0 - 4, x0 + 132) -- are staged once with coalesced 16-byte loads;
-// each sample then reads shared memory at a compile-time row pitch. Samples, their order
-// and every point's arithmetic are those of k_lincomb_ring, so both kernels give the same
-// bits. The staging layout comes from the host (LaunchDesc::smo / sfy / sfn / sfo).
-constexpr int kSmemPitch = kStagePitch;            // floats per staged row
-constexpr int kSmemVec = kSmemPitch / 4;           // float4 per staged row
-static_assert(kSmemPitch == kThreadsX + 8, "staged rows cover the block's columns and 4 on each side");
-
-template <int R, int M>
-__global__ void __launch_bounds__(kThreadsX) k_lincomb_smem(const __grid_constant__ LaunchDesc d)
-{
-    extern __shared__ float4 sm4[];
-    float* sm = reinterpret_cast<float*>(sm4);
-    const int x0 = d.lo[0] + (int)blockIdx.x * kThreadsX;
-    const int r0 = (int)blockIdx.z * R;
-    const int nr = d.hi[1] - d.lo[1] - r0;
-    const int nrv = nr < R ? nr : R;                // valid output rows of this tile
-    for (int j = 1; j < d.nargs; ++j) {
-        const int ny = d.sfn[j];
-        if (ny <= 0) continue;
-        const DView& v = d.v[j];
-        const int rows = nrv + (ny - R);             // staged rows this tile needs
-        const float* fb = reinterpret_cast<const float*>(v.base) + v.ox + x0 - 4;
-        float4* dst = sm4 + d.sfo[j] * kSmemVec;
-        const int s_first = d.lo[1] + r0 + d.sfy[j];
-        const int xlo = -v.ox, xhi = (int)v.pitch - v.ox;   // addressable columns of a row
-        for (int i = threadIdx.x; i < rows * kSmemVec; i += kThreadsX) {
-            const int rr = i / kSmemVec, c = i - rr * kSmemVec;
-            int slot = v.slot0 + (s_first + rr - v.W0);
-            if (slot >= v.S) slot -= v.S;
-            const int xs = x0 - 4 + 4 * c;
-            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (xs >= xlo && xs + 4 <= xhi)
-                val = __ldg(reinterpret_cast<const float4*>(fb + slot * (int)v.row_elems + 4 * c));
-            dst[rr * kSmemVec + c] = val;
-        }
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= d.hi[0]) return;
-    const float* cp = d.paramsf;
-    float acc[R], xa[R], xb[R], xc[R];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const float c = cp[1 + m];
-        const float* sp = sm + d.smo[m] + threadIdx.x;
-        float val[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) val[r] = (R <= nr || r < nr) ? sp[r * kSmemPitch] : 0.f;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (m == 0) { acc[r] = c * val[r]; xa[r] = val[r]; }
-            else {
-                acc[r] = fma_t(c, val[r], acc[r]);
-                if (m == 1) xb[r] = val[r];
-                if (m == 2) xc[r] = val[r];
-            }
-        }
-    }
-    const float alpha = cp[0];
-    if (alpha != 0.f) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float a = xa[r];
-            const float b = M > 1 ? xb[r] : xa[r];
-            const float c = M > 2 ? xc[r] : xa[r];
-            acc[r] = acc[r] + nl_div((alpha * a) * b, 1.f + c * c);
-        }
-    }
-    const SampleRec& od = d.orec;
-    float* op = const_cast<float*>(reinterpret_cast<const float*>(od.p0)) + x;
-    int rel = od.sl0 + r0;
-    if (rel >= od.S) rel -= od.S;
-    const int re = d.ore;
-    float* q = op + rel * re;
-    const int w = od.S - rel;
-    const int sre = od.S * re;
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (R <= nr || r < nr) q[r * re - (r >= w ? sre : 0)] = acc[r];
-}
-
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreadsX) k_copy_lean(const __grid_constant__ LaunchDesc d)
 {
@@ -612,16 +528,6 @@ int ring_rows_for(const LaunchDesc& d)
 template <typename T, int M>
 cudaError_t lincomb_m(const LaunchDesc& d, cudaStream_t st)
 {
-    if constexpr (M > 0 && std::is_same<T, float>::value) {
-        if (d.smem_bytes > 0) {
-            const int sa = d.ndim - 1;
-            const int nx = d.hi[0] - d.lo[0], ns = d.hi[sa] - d.lo[sa];
-            if (nx <= 0 || ns <= 0) return cudaSuccess;
-            dim3 grid((nx + kThreadsX - 1) / kThreadsX, 1, (ns + kStageRows - 1) / kStageRows);
-            k_lincomb_smem<kStageRows, M><<<grid, kThreadsX, d.smem_bytes, st>>>(d);
-            return cudaGetLastError();
-        }
-    }
     if constexpr (M > 0) {
         if (d.ring) {
             if (ring_rows_for<T, M>(d) == 4) return launch_rows(d, st, k_lincomb_ring<T, 4, M>, 4);

@@ -9,11 +9,6 @@ namespace oc {
 
 constexpr int kLaunchMaxArgs = 40;
 constexpr int kLaunchMaxSamples = 64;
-// shared-memory LINCOMB staging: rows per block and staged row pitch (floats) for a block
-// of 128 x-columns with samples up to 4 columns away
-constexpr int kStageRows = 8;
-constexpr int kStagePitch = 136;
-constexpr int kStageMaxBytes = 48 * 1024;
 
 // Device view of one dataset argument inside one launch. A slow row s lives at
 // slab slot  slot0 + (s - W0)  (minus S if >= S); every row a launch touches lies in
@@ -71,14 +66,6 @@ struct LaunchDesc {
     int sre[kLaunchMaxSamples];// sample row strides in elements (ring launches)
     SampleRec orec;            // output argument (arg 0) of LINCOMB / COPY
     SampleRec srec[kLaunchMaxSamples];
-    // shared-memory staging of a 2-D FP32 ring LINCOMB (smem_bytes > 0): input argument j
-    // stages sfn[j] rows (the tile's rows plus its slow-axis sample span), starting sfy[j]
-    // rows from the tile's first row, at staged-row offset sfo[j]; sample m reads staged
-    // element smo[m] + the thread's column (+ row * pitch). Rows of kThreadsX + 8 floats
-    // cover columns x0 - 4 .. x0 + kThreadsX + 3 of a tile starting at x0.
-    int smem_bytes;
-    short sfy[kLaunchMaxArgs], sfn[kLaunchMaxArgs], sfo[kLaunchMaxArgs];
-    short smo[kLaunchMaxSamples];
 };
 
 // Strided host-to-device copies done by SM threads that read the pinned host store

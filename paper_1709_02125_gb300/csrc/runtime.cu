@@ -400,7 +400,8 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                 int di = P.dat_index[ar.dat];
                 int W0 = (ar.access == OC_READ || ar.access == OC_RW) ? s + ar.rmin[sa] : s;
                 if (ar.access == OC_RW) W0 = std::min(W0, s);
-                d.v[j] = make_view(dd, slab_base(P, di), P.dp[di].S, W0);
+                // a managed store is addressed in place: every row at its own slot
+                d.v[j] = make_view(dd, slab_base(P, di), dd.managed ? dd.nrows : P.dp[di].S, W0);
                 if (ar.access == OC_READ && j >= 1)
                     for (auto& o : ar.off) {
                         if (ns < kLaunchMaxSamples) {
@@ -442,37 +443,6 @@ static void build_descs(const Plan& P, const std::vector<Loop>& loops,
                         d.ring = 1;
                         d.ore = (int)d.orec.row_elems;
                         for (int m = 0; m < ns; ++m) d.sre[m] = (int)d.srec[m].row_elems;
-                    }
-                    // 2-D FP32 LINCOMB with x offsets within 4 and a 16-byte aligned first
-                    // column: shared-memory staging of the input rows (k_lincomb_smem)
-                    if (ok && lp.kernel == OC_K_LINCOMB && lp.ndim == 2 && d.dtype == OC_F32 && ns <= 20 &&
-                        (lp.lo[0] & 3) == 0) {
-                        int ymin[kLaunchMaxArgs], ymax[kLaunchMaxArgs];
-                        for (int j = 0; j < d.nargs; ++j) { ymin[j] = INT_MAX; ymax[j] = INT_MIN; d.sfn[j] = 0; }
-                        bool fit = true;
-                        for (int m = 0; m < ns; ++m) {
-                            const int j = d.sarg[m];
-                            if (d.soff[m][0] < -4 || d.soff[m][0] > 4) fit = false;
-                            ymin[j] = std::min(ymin[j], d.soff[m][1]);
-                            ymax[j] = std::max(ymax[j], d.soff[m][1]);
-                        }
-                        int rows = 0;
-                        for (int j = 1; j < d.nargs && fit; ++j) {
-                            if (ymin[j] > ymax[j]) continue;
-                            if (ymax[j] - ymin[j] > 8) fit = false;
-                            d.sfy[j] = (short)ymin[j];
-                            d.sfn[j] = (short)(kStageRows + ymax[j] - ymin[j]);
-                            d.sfo[j] = (short)rows;
-                            rows += d.sfn[j];
-                        }
-                        const long long bytes = (long long)rows * kStagePitch * 4;
-                        if (fit && bytes <= kStageMaxBytes) {
-                            for (int m = 0; m < ns; ++m) {
-                                const int j = d.sarg[m];
-                                d.smo[m] = (short)((d.sfo[j] + d.soff[m][1] - ymin[j]) * kStagePitch + d.soff[m][0] + 4);
-                            }
-                            d.smem_bytes = (int)bytes;
-                        }
                     }
                 }
             }

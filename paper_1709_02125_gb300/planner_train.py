@@ -10,8 +10,9 @@ The network is a cost model of two alternatives A0, A1 to the fixed rule: its ta
 y_k = log2(t(fixed) / t(A_k)), clipped to [-2, 2]. The alternatives are chosen on the
 training split alone: the twelve pairs of candidates (largest or 3/4 height, depth 3 or 4,
 any residency level) that a perfect predictor would gain most with (mean over the chains
-of max(0, y0, y1)) are shortlisted, and the pair whose trained network has the lowest
-regret in a 3-fold cross-validation over the training chains is kept. The planner keeps the fixed
+of max(0, y0, y1)) and every pair of residency levels at the fixed tiling are
+shortlisted, and the pair whose trained network has the lowest regret in a 3-fold
+cross-validation over the training chains is kept. The planner keeps the fixed
 rule unless an alternative is predicted to win by more than MARGIN (log2 units), then
 takes the one with the larger predicted gain. Features are standardised with the
 training split's mean and deviation. Training runs on the GPU through liboc's MLP kernels
@@ -106,7 +107,12 @@ def shortlist(rows, k=12):
     scored = [(float(np.mean(np.maximum(0.0, np.maximum(G[a], G[b])))), (a, b))
               for a, b in itertools.combinations(cands, 2)]
     scored.sort(key=lambda t: -t[0])
-    return [pair for _, pair in scored[:k]]
+    out = [pair for _, pair in scored[:k]]
+    # every pair of residency levels at the fixed tiling is a candidate too: residency is
+    # what the fixed rule lacks most on link-bound chains
+    res_only = [c for c in cands if c[0] == 0 and c[1] == 3 and c[2] > 0]
+    out += [pair for pair in itertools.combinations(res_only, 2) if pair not in out]
+    return out
 
 
 def alternatives(rows):

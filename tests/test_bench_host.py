@@ -90,6 +90,19 @@ def test_kernel_symbol(name, dtype, sym):
     assert bench.kernel_symbol(name, dtype) == sym
 
 
+def test_recorded_traffic_dropped_for_another_plan(tmp_path, monkeypatch):
+    """A launch's DRAM bytes follow its rows: a record taken at one tile height (or set of
+    resident datasets) is not reported for a run with another."""
+    _traffic_root(tmp_path, "x = a + b;\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    p = tmp_path / "profiles" / "traffic.json"
+    rec = json.loads(p.read_text())
+    rec["random/mixed_learned"].update({"tile_height": 256, "resident_dats": 5})
+    p.write_text(json.dumps(rec))
+    assert bench.recorded_traffic("random", "mixed_learned", {"tile_height": 256, "resident_dats": 5}) is not None
+    assert bench.recorded_traffic("random", "mixed_learned", {"tile_height": 410, "resident_dats": 0}) is None
+
+
 def test_committed_traffic_record_points_at_real_markers():
     """The committed record names a source file and two markers that exist in it, in
     order (whether the hash still matches is the bench's decision at run time)."""
