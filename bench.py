@@ -183,7 +183,8 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
         # fixed-dt mode: `spc` steps per chain and no reduction in the chain; dt is half
         # the CFL step of the initial state, computed once before the timed steps
         from workloads import euler
-        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed, steps=spc)
+        # FP64: the in-place form, the same chain every step (the cyclic flag's promise)
+        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed, steps=spc, inplace=True)
         from workloads.spec import RedSpec
         reds = [RedSpec("dtmin", "min")]
 
@@ -194,7 +195,7 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
                 if state["dt"] is None:
                     ex.enqueue(euler.dt_loop(n, mixed))
                     state["dt"] = 0.5 * euler.CFL * ex.reduce("dtmin")
-                loops, state["src"] = euler.fixed_dt_chain(n, state["dt"], spc, mixed, state["src"])
+                loops, state["src"] = euler.fixed_dt_chain(n, state["dt"], spc, mixed, state["src"], inplace=True)
                 for lp in loops:
                     ex.enqueue(lp)
                 ex.flush()
@@ -204,23 +205,22 @@ def build_workload(name: str, mixed: bool, n: int, spc: int = 1):
         return dats, reds, make_step, fp, n * n * spc
     if name == "euler":
         from workloads import euler
-        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed)
+        # FP64: the in-place form, the same chain every step (the cyclic flag's promise)
+        dats = euler.datasets(n, "f32" if mixed else "f64", euler.initial(n), mixed, inplace=True)
         from workloads.spec import RedSpec
         reds = [RedSpec("dtmin", "min")]
 
         def make_step(ex):
-            state = {"src": "A", "dst": "B", "dtmin": None}
+            state = {"dtmin": None}
 
             def step():
                 if state["dtmin"] is None:
                     ex.enqueue(euler.dt_loop(n, mixed))
                     state["dtmin"] = ex.reduce("dtmin")
                 dt = euler.CFL * state["dtmin"]
-                for lp in euler.chain_loops(n, dt, state["src"], state["dst"], mixed):
+                for lp in euler.chain_loops(n, dt, "A", "A", mixed, inplace=True):
                     ex.enqueue(lp)
                 state["dtmin"] = ex.reduce("dtmin")
-                if not mixed:
-                    state["src"], state["dst"] = state["dst"], state["src"]
                 return [state["dtmin"]]
             return step
         fp = sum(int(np.prod(d.shape)) * (4 if d.dtype == "f32" else 8) for d in dats)

@@ -68,8 +68,11 @@ extern "C" {
 /* ---- context flags (oc_init / oc_set_flag) ----------------------------------
  * OC_FLAG_CYCLIC   Sec. 4.1 "cyclic" optimisation: datasets whose first access in a
  *                  chain is a write are treated as per-chain temporaries and are
- *                  never downloaded. UNSAFE if such a dataset is read by a later
- *                  chain or fetched: its host copy is then stale. Off by default.
+ *                  never downloaded by a streamed plan (resident datasets and managed
+ *                  stores keep their values). Their host copy is then stale: oc_fetch_dat
+ *                  returns unspecified values for them, and a later chain that reads one
+ *                  before writing it fails with OC_ERR_STATE (nothing of it runs) until a
+ *                  chain writes the dataset without skipping its download. Off by default.
  * OC_FLAG_PREFETCH Sec. 4.1 speculative prefetch: while the last tile of a chain
  *                  runs, upload the first tile of the next chain assuming it has
  *                  the same plan; the next chain uploads only what is missing.

@@ -351,21 +351,22 @@ __device__ __forceinline__ double red_mode(double v, int mode)
     return mode == 1 ? fabs(v) : (mode == 2 ? v * v : v);
 }
 
-// Fold n consecutive elements pa[0..n) (+ pb[0..n) when pb is set) into this thread's
+// Fold n consecutive elements pa[0..n) (+ pb[0..n) when pb is set) into this lane's
 // accumulator: a scalar head up to the first 16-byte boundary of pa, 16-byte vectors,
-// a scalar tail. Thread k of the block takes head element k, vectors k, k + 256, ...
-// and tail element k (+ 256...), each in that order, so the association is fixed by the
-// segment alone. Both sources go vector only if they share their offset modulo 16.
+// a scalar tail. Lane k of the warp takes head element k, vectors k, k + 32, ... and tail
+// element k (+ 32...), each in that order, so the association is fixed by the segment
+// alone. Both sources go vector only if they share their offset modulo 16.
 template <typename T>
 __device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mode, int op, double& acc)
 {
+    const int lane = (int)threadIdx.x & 31;
     using V = typename VecOf<T>::V;
     constexpr int N = VecOf<T>::N;
     const uintptr_t ua = reinterpret_cast<uintptr_t>(pa);
     const bool vec = (ua % sizeof(T)) == 0 && (!pb || ((reinterpret_cast<uintptr_t>(pb) ^ ua) & 15) == 0);
     int head = vec ? (int)(((16 - (ua & 15)) & 15) / sizeof(T)) : n;
     if (head > n) head = n;
-    for (int i = threadIdx.x; i < head; i += kRedThreads) {
+    for (int i = lane; i < head; i += 32) {
         double v = (double)__ldg(pa + i);
         if (pb) v = v + (double)__ldg(pb + i);
         acc = red_apply(op, acc, red_mode(v, mode));
@@ -373,7 +374,7 @@ __device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mo
     const int nv = (n - head) / N;
     const V* va = reinterpret_cast<const V*>(pa + head);
     const V* vb = reinterpret_cast<const V*>(pb ? pb + head : pa);
-    for (int i = threadIdx.x; i < nv; i += kRedThreads) {
+    for (int i = lane; i < nv; i += 32) {
         T ea[N], eb[N];
         *reinterpret_cast<V*>(ea) = __ldg(va + i);
         if (pb) *reinterpret_cast<V*>(eb) = __ldg(vb + i);
@@ -384,20 +385,24 @@ __device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mo
             acc = red_apply(op, acc, red_mode(v, mode));
         }
     }
-    for (int i = head + nv * N + threadIdx.x; i < n; i += kRedThreads) {
+    for (int i = head + nv * N + lane; i < n; i += 32) {
         double v = (double)__ldg(pa + i);
         if (pb) v = v + (double)__ldg(pb + i);
         acc = red_apply(op, acc, red_mode(v, mode));
     }
 }
 
-// One block per (chunk of kRedPoints points of a slow row, group of slow rows): block
-// (c, g) folds chunk c of rows s = lo + g, lo + g + gridDim.y, ... The points of a row
-// are its x-lines in order (one line in 2-D, the y-lines of a z-plane in 3-D), so chunk c
+// One warp per (chunk of kRedPoints points of a slow row, slow row): blocks of
+// kRedThreads / 32 warps; warp w of block (c, g) folds chunk c of rows
+// s = lo + g * W + w, then + gridDim.y * W ... (W warps per block). The points of a row are
+// its x-lines in order (one line in 2-D, the y-lines of a z-plane in 3-D), so chunk c
 // covers whole or partial lines; each line segment is contiguous (a REDUCE reads at
-// offset 0 inside the range, which never wraps a periodic axis). The partial of row s,
-// chunk c is stored at part[(s - part_row0) * chunks + c], independent of the tiling, so
-// tiled and untiled runs fold the same partials in the same order.
+// offset 0 inside the range, which never wraps a periodic axis). A warp has 32 lanes'
+// worth of 16-byte loads in flight per segment and folds with a fixed shuffle tree; the
+// partial of row s, chunk c is stored at part[(s - part_row0) * chunks + c], independent
+// of the tiling, so tiled and untiled runs fold the same partials in the same order.
+constexpr int kRedWarps = kRedThreads / 32;
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ LaunchDesc d)
 {
@@ -412,10 +417,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ 
     const bool two = d.nargs == 3;
     const DView& a = d.v[0];
     const DView& b = d.v[1];
-    // lines touched by the chunk: one division per block
+    // lines touched by the chunk: one division per warp
     const int l0 = q1 > q0 ? (int)(q0 / nxr) : 0;
     const int l1 = q1 > q0 ? (int)((q1 - 1) / nxr) : -1;
-    for (int s = d.lo[sa] + (int)blockIdx.y; s < d.hi[sa]; s += (int)gridDim.y) {
+    const int w = (int)threadIdx.x >> 5;
+    for (int s = d.lo[sa] + (int)blockIdx.y * kRedWarps + w; s < d.hi[sa]; s += (int)gridDim.y * kRedWarps) {
         const long long ra = (long long)first_slot(a, s) * a.row_elems;
         const long long rb = two ? (long long)first_slot(b, s) * b.row_elems : 0;
         double acc = red_identity(op);
@@ -428,9 +434,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ 
             const T* pb = two ? col_ptr<T>(b, d.lo[0] + x0, yl) + rb : nullptr;
             seg_fold<T>(pa, pb, x1 - x0, mode, op, acc);
         }
-        acc = block_fold(acc, op);
-        if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
-        __syncthreads();   // block_fold's shared slots are reused by the next row
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
+        if ((threadIdx.x & 31) == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
     }
 }
 
@@ -570,7 +576,7 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
         const int sa = d.ndim - 1;
         const int ns = d.hi[sa] - d.lo[sa];
         if (ns <= 0) return cudaSuccess;
-        dim3 grid(d.chunks, std::min(ns, 65535), 1);
+        dim3 grid(d.chunks, std::min((ns + kRedWarps - 1) / kRedWarps, 65535), 1);
         if (f32) k_reduce<float><<<grid, kRedThreads, 0, st>>>(d);
         else k_reduce<double><<<grid, kRedThreads, 0, st>>>(d);
         return cudaGetLastError();

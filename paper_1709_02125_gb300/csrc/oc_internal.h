@@ -40,6 +40,9 @@ struct Dat {
     long long res_off = -1;
     bool dev_valid = false;   // device copy current
     bool host_valid = true;   // host copy current
+    // written first by a streamed chain under the cyclic flag: its rows were not
+    // downloaded, so the host store no longer holds its values (Sec. 4.1)
+    bool cyc_stale = false;
     int slow() const { return ndim - 1; }
     long long row_bytes() const { return row_elems * esz; }
     long long bytes() const { return (long long)nrows * row_bytes(); }

@@ -271,6 +271,13 @@ static int copy_rows(const Dat& d, char* slab, int S, int a, int b, bool up, cud
     if (!strip_s) strip_s = s;
     const long long rb = d.row_bytes();
     const size_t lp = (size_t)d.pitch * d.esz;
+    // the host store holds rows [y0, y0 + nrows) only: a row range outside it is a
+    // planning error, reported before any copy touches memory outside the store
+    if (!host_override && a < b && (a < d.y0 || b > d.y0 + d.nrows))
+        return fail(OC_ERR_STATE, "%s copy of rows [%d, %d) outside the host store's rows [%d, %d)",
+                    up ? "upload" : "download", a, b, d.y0, d.y0 + d.nrows);
+    if (S <= 0 || (x0 < x1 && (x0 < -d.hlo[0] || x1 > d.size[0] + d.hhi[0])))
+        return fail(OC_ERR_STATE, "copy of rows [%d, %d): slab of %d rows, columns [%d, %d)", a, b, S, x0, x1);
     while (a < b) {
         int slot = (int)(((long long)(a - d.y0)) % S);
         int n = std::min(b - a, S - slot);
@@ -770,6 +777,9 @@ static int ghost_fill_host(const Dat& d)
     char* h = (char*)d.host;
     auto row = [&](int y) { return h + (long long)(y - d.y0) * rb; };
     const int ng = lo + hi;
+    if (-lo < d.y0 || n + hi > d.y0 + d.nrows)
+        return fail(OC_ERR_STATE, "periodic ghost rows [%d, %d) outside the host store's rows [%d, %d)",
+                    -lo, n + hi, d.y0, d.y0 + d.nrows);
     auto fill = [&](int k0, int k1) {
         for (int k = k0; k < k1; ++k) {
             const int y = k < lo ? k - lo : n + (k - lo);
@@ -794,12 +804,16 @@ static int ghost_fill_host(const Dat& d)
     return OC_OK;
 }
 
-static int ghost_fill_device(const Dat& d, cudaStream_t s)
+// Deep ghost rows of a dataset held whole in the arena at byte offset `off` (in-core or
+// resident), refreshed on the device.
+static int ghost_fill_device(const Dat& d, long long off, cudaStream_t s)
 {
     const int sa = d.slow();
     const int n = d.size[sa], lo = d.hlo[sa], hi = d.hhi[sa];
     const long long rb = d.row_bytes();
-    char* b = g->arena + d.res_off;
+    if (off < 0 || off + d.bytes() > g->arena_bytes)
+        return fail(OC_ERR_STATE, "ghost refresh of dataset outside the arena (offset %lld)", off);
+    char* b = g->arena + off;
     auto row = [&](int y) { return b + (long long)(y + lo) * rb; };
     // ghost row y takes interior row y mod n: runs of consecutive rows, one copy each
     auto fill = [&](int y, int end) -> int {
@@ -1254,7 +1268,10 @@ static int run_plan(Plan& P, const std::vector<Loop>& loops, bool trial, double*
         if (!P.incore)
             for (size_t di = 0; di < P.dp.size(); ++di) {
                 const Dat& d = g->dats[P.dp[di].dat];
-                if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+                if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
+                    const int r = ghost_fill_host(d);
+                    if (r) return r;
+                }
             }
         if (P.res_dats > 0)
             for (const Loop& lp : loops)
@@ -1342,7 +1359,7 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
         for (size_t di = 0; di < P.dp.size(); ++di) {
             Dat& d = g->dats[P.dp[di].dat];
             if ((d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
-                rc = ghost_fill_device(d, s0);
+                rc = ghost_fill_device(d, d.res_off, s0);
                 if (rc) return rc;
             }
         }
@@ -1359,7 +1376,10 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
     } else {
         for (size_t di = 0; di < P.dp.size(); ++di) {
             const Dat& d = g->dats[P.dp[di].dat];
-            if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) ghost_fill_host(d);
+            if (!P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
+                rc = ghost_fill_host(d);
+                if (rc) return rc;
+            }
         }
         // datasets the plan keeps resident: uploaded whole while their device copy is not
         // current (a trial uploaded them before its timing started), deep ghosts refreshed
@@ -1382,7 +1402,8 @@ static int issue_chain(Plan& P, const std::vector<Loop>& loops, bool trial, bool
             for (size_t di = 0; di < P.dp.size(); ++di) {
                 const Dat& d = g->dats[P.dp[di].dat];
                 if (P.dp[di].resident && (d.periodic & (1 << d.slow())) && reads_ghosts(P, (int)di)) {
-                    rc = ghost_fill_device(d, s0);
+                    // the plan's offset: a trial runs without applying the residency
+                    rc = ghost_fill_device(d, P.dp[di].off, s0);
                     if (rc) return rc;
                 }
             }
@@ -1573,6 +1594,45 @@ static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, boo
     return OC_OK;
 }
 
+// The cyclic flag (Sec. 4.1) is a promise that the chain is the one repeated: a dataset
+// it writes before reading is a temporary, so a streamed plan never downloads it and its
+// host rows keep older values. A later chain that reads such a dataset before writing it
+// breaks the promise and would compute from those rows; it is refused instead. A device
+// copy that is current (in-core or resident datasets) is the dataset's value and needs no
+// host rows, and a managed store is one copy, so neither is affected.
+static int cyclic_guard(const Plan& P, const std::vector<Loop>& loops)
+{
+    const size_t ND = g->dats.size();
+    std::vector<uint8_t> first(ND, 0), written(ND, 0);   // first: 1 written first, 2 read first
+    for (const Loop& lp : loops) {
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && (ar.access == OC_READ || ar.access == OC_RW) && !first[ar.dat])
+                first[ar.dat] = 2;
+        for (const Arg& ar : lp.args)
+            if (ar.access != OC_REDUCE && (ar.access == OC_WRITE || ar.access == OC_RW)) {
+                if (!first[ar.dat]) first[ar.dat] = 1;
+                written[ar.dat] = 1;
+            }
+    }
+    for (size_t k = 0; k < ND; ++k) {
+        const Dat& d = g->dats[k];
+        if (first[k] != 2 || !d.cyc_stale || d.managed) continue;
+        const bool on_dev = P.incore ? (d.resident && d.dev_valid)
+                                     : (P.dat_index[k] >= 0 && P.dp[P.dat_index[k]].resident && d.resident &&
+                                        d.dev_valid && d.res_off == P.dp[P.dat_index[k]].off);
+        if (!on_dev)
+            return fail(OC_ERR_STATE,
+                        "dataset %zu is read before it is written, but an earlier chain wrote it first under "
+                        "the cyclic flag and did not download it: the chain is not the repeated one", k);
+    }
+    // a dataset this chain writes is stale afterwards exactly when its download is skipped
+    const bool skips = (g->flags & OC_FLAG_CYCLIC) && !P.incore && !(g->flags & OC_FLAG_MANAGED);
+    for (size_t k = 0; k < ND; ++k)
+        if (written[k])
+            g->dats[k].cyc_stale = skips && first[k] == 1 && P.dat_index[k] >= 0 && !P.dp[P.dat_index[k]].resident;
+    return OC_OK;
+}
+
 static int execute()
 {
     if (g->queue.empty()) return OC_OK;
@@ -1606,6 +1666,8 @@ static int execute()
             if (ar.access != OC_REDUCE)
                 S.hbm_bytes += pts * g->dats[ar.dat].esz * (ar.access == OC_RW ? 2 : 1);
     }
+    rc = cyclic_guard(P, loops);
+    if (rc) return rc;
     if (g->dryrun) {
         S.seconds = 0;
         S.chains++;

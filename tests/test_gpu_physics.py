@@ -23,11 +23,11 @@ def built():
     __graft_entry__.build()
 
 
-def euler_gpu(n, steps, budget, mixed=False, h=0, flags=0, totals=False):
+def euler_gpu(n, steps, budget, mixed=False, h=0, flags=0, totals=False, inplace=False):
     from paper_1709_02125_gb300 import oc
     with oc.Executor(budget, flags=flags) as ex:
         ex.set_tiling(h, 3 if h else 0)
-        dts, pre, tots = euler.run(ex, n, steps, mixed=mixed, totals=totals)
+        dts, pre, tots = euler.run(ex, n, steps, mixed=mixed, totals=totals, inplace=inplace)
         st = ex.stats()
         U = np.stack([ex.fetch(f"{pre}_{k}")[2:n + 2].astype(np.float64) for k in EU])
         if mixed:
@@ -57,6 +57,27 @@ def test_euler_fp64_tiled_untiled_oracle(oracle_lib):
     Ut, dtt, stt, _ = euler_gpu(n, steps, fp // 3)
     assert sti["tiles"] == 1 and stt["tiles"] > 1
     assert np.array_equal(Ui, Ut) and dti == dtt
+    Uo, dto = euler_oracle(n, steps)
+    for k in range(4):
+        assert rel_max(Ut[k], Uo[k]) <= 1e-12, EU[k]
+    assert np.allclose(dtt, dto, rtol=1e-12, atol=0)
+
+
+def test_euler_fp64_in_place_form_under_cyclic(oracle_lib):
+    """The FP64 in-place form (A += D, the same chain every step) with cyclic + prefetch +
+    graphs at a third of the footprint: bit-identical to its untiled run, within 1e-12 of
+    the oracle's direct MacCormack update, and its intermediates never leave the device."""
+    from paper_1709_02125_gb300 import oc
+    n, steps = 200, 4
+    fp = footprint(euler.datasets(n, inplace=True))
+    flags = oc.OC_FLAG_CYCLIC | oc.OC_FLAG_PREFETCH | oc.OC_FLAG_GRAPHS
+    Ui, dti, sti, _ = euler_gpu(n, steps, 4 * fp, inplace=True)
+    Ut, dtt, stt, _ = euler_gpu(n, steps, fp // 3, flags=flags, inplace=True)
+    assert sti["tiles"] == 1 and stt["tiles"] > 1
+    assert np.array_equal(Ui, Ut) and dti == dtt
+    # one chain downloads the conserved state only: 4 datasets of at most n + 4 rows
+    # of (padded) x-lines of n points
+    assert stt["d2h_bytes"] <= 4 * (n + 4) * (n + 8) * 8
     Uo, dto = euler_oracle(n, steps)
     for k in range(4):
         assert rel_max(Ut[k], Uo[k]) <= 1e-12, EU[k]

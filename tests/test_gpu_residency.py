@@ -104,3 +104,25 @@ def test_residency_periodic_slow_axis():
     (Ui, dti, sti), (Ur, dtr, str_) = out
     assert sti["tiles"] == 1 and str_["tiles"] > 1 and str_["resident_dats"] > 0
     assert np.array_equal(Ui, Ur) and dti == dtr
+
+
+def test_autotune_trials_of_periodic_resident_plans():
+    """The autotuner times plans that keep periodic datasets resident before any of them
+    is made resident: the trials refresh those datasets' deep ghosts at the plan's own
+    arena offsets. Euler with the autotuner at a third of the footprint equals the untiled
+    run bit for bit, and the trials included resident plans."""
+    from paper_1709_02125_gb300 import oc
+    n, steps = 200, 3
+    fp = sum(np.prod(d.shape) * 8 for d in euler.datasets(n))
+    out = []
+    for budget, planner in ((4 * fp, oc.OC_PLAN_FIXED), (fp // 3, oc.OC_PLAN_AUTOTUNE)):
+        with oc.Executor(int(budget), planner=planner) as ex:
+            dts, pre, _ = euler.run(ex, n, steps)
+            st = ex.stats()
+            tune = ex.autotune_result() if planner == oc.OC_PLAN_AUTOTUNE else None
+            U = np.stack([ex.fetch(f"{pre}_{k}") for k in ("r", "mx", "my", "E")])
+        out.append((U, dts, st, tune))
+    (Ui, dti, sti, _), (Ua, dta, sta, tune) = out
+    assert sti["tiles"] == 1 and sta["tiles"] > 1
+    assert tune is not None and np.any(tune[:, 5] > 0)   # residency levels were tried
+    assert np.array_equal(Ui, Ua) and dti == dta

@@ -9,7 +9,12 @@ dissipation eps4 = 1/64.
 `chain_loops` is the user code of one time step as a loop chain for the executor:
 34 datasets -- two sets of conserved variables (ping-pong), primitives, fluxes,
 predicted state, its primitives and fluxes -- and 7 loops per step, the last being the
-CFL min-reduction that ends the chain. x is periodic inside each row (kernels wrap);
+CFL min-reduction that ends the chain. The FP64 in-place form (`inplace=True`) keeps one
+set of conserved variables A and an increment set D instead: the corrector writes the
+increment and four pointwise LINCOMB loops add it (A = 1*A + 1*D, no nonlinear term), so
+every step is the same chain -- the repeated chain the cyclic flag asks for, under which
+the increments and the other intermediates are never downloaded. The mixed form is in
+place already (compensated hi + lo update). x is periodic inside each row (kernels wrap);
 y, the tiled axis, is periodic through halo rows refreshed at the start of every
 chain (deep ghosts), into which the loops extend their ranges.
 """
@@ -46,7 +51,7 @@ def initial(n: int, edge: float = 1.5) -> np.ndarray:
 
 
 def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = False,
-             steps: int = 1) -> List[DatSpec]:
+             steps: int = 1, inplace: bool = False) -> List[DatSpec]:
     """Datasets of the chain. Conserved sets have 2 ghost rows per step of the chain in
     y (one step reads U at y +- 2); the intermediates one row more than the widest range
     a loop computes them over."""
@@ -72,6 +77,9 @@ def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = Fa
             dat(f"A_{c}", gc, gc, hi)
             dat(f"L_{c}", gc, gc, lo)
             dat(f"D_{c}", gc - 2, gc - 2)
+        elif inplace:
+            dat(f"A_{c}", gc, gc, init)
+            dat(f"D_{c}", gc - 2, gc - 2)
         else:
             dat(f"A_{c}", gc, gc, init)
             dat(f"B_{c}", gc, gc)
@@ -89,10 +97,13 @@ def datasets(n: int, dtype: str = "f64", U0: np.ndarray = None, mixed: bool = Fa
 
 
 def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool = False,
-                red: str = "dtmin", ext: int = 0, with_dt: bool = True) -> List[Loop]:
-    """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L),
-    computing the new state over rows [-ext, n + ext) (ghost rows a later step of the
-    same chain reads), optionally followed by the CFL min-reduction."""
+                red: str = "dtmin", ext: int = 0, with_dt: bool = True, inplace: bool = False) -> List[Loop]:
+    """One MacCormack step U_src -> U_dst (mixed: in-place compensated update of A/L;
+    FP64 with `inplace`: A += D, src and dst ignored), computing the new state over rows
+    [-ext, n + ext) (ghost rows a later step of the same chain reads), optionally followed
+    by the CFL min-reduction."""
+    if inplace and not mixed:
+        src = dst = "A"
     lx = ly = dt / (1.0 / n)
     c = ["r", "mx", "my", "E"]
     U = [f"{src}_{k}" for k in c]
@@ -118,7 +129,16 @@ def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool =
     corr_in = ([Arg(u, READ, cross) for u in U] + [Arg(s, READ) for s in S] +
                [Arg(f"H{k}", READ, [(0, 0), (-1, 0)]) for k in range(4)] +
                [Arg(f"K{k}", READ, [(0, 0), (0, -1)]) for k in range(4)])
-    if not mixed:
+    if inplace and not mixed:
+        loops.append(Loop("euler_corr", (0, -e), (n, n + e), corr_in + [Arg(f"D_{k}", WRITE) for k in c],
+                          [lx, ly, EPS4, 1.0]))
+        for k in c:
+            loops.append(Loop("lincomb", (0, -e), (n, n + e), [Arg(f"A_{k}", WRITE), Arg(f"A_{k}", READ, [(0, 0)]),
+                                                              Arg(f"D_{k}", READ, [(0, 0)])], [0.0, 1.0, 1.0]))
+        if with_dt:
+            loops.append(Loop("euler_dt", (0, 0), (n, n), [Arg(f"A_{k}", READ) for k in c] + [Arg(red, REDUCE)],
+                              [GAMMA, 1.0 / n, 1.0 / n]))
+    elif not mixed:
         loops.append(Loop("euler_corr", (0, -e), (n, n + e), corr_in + [Arg(f"{dst}_{k}", WRITE) for k in c],
                           [lx, ly, EPS4, 0.0]))
         if with_dt:
@@ -136,7 +156,8 @@ def chain_loops(n: int, dt: float, src: str = "A", dst: str = "B", mixed: bool =
     return loops
 
 
-def fixed_dt_chain(n: int, dt: float, steps: int, mixed: bool = False, src: str = "A") -> Tuple[List[Loop], str]:
+def fixed_dt_chain(n: int, dt: float, steps: int, mixed: bool = False, src: str = "A",
+                   inplace: bool = False) -> Tuple[List[Loop], str]:
     """`steps` MacCormack steps of one fixed dt as one chain with no reduction (the
     multi-timestep chains of Sec. 5.3); step j computes its new state over the ghost
     rows the remaining steps read, 2 per step. Datasets: datasets(..., steps=steps).
@@ -144,10 +165,10 @@ def fixed_dt_chain(n: int, dt: float, steps: int, mixed: bool = False, src: str 
     loops: List[Loop] = []
     a, b = src, ("B" if src == "A" else "A")
     for j in range(steps):
-        loops += chain_loops(n, dt, a, b, mixed, ext=2 * (steps - 1 - j), with_dt=False)
-        if not mixed:
+        loops += chain_loops(n, dt, a, b, mixed, ext=2 * (steps - 1 - j), with_dt=False, inplace=inplace)
+        if not (mixed or inplace):
             a, b = b, a
-    return loops, ("A" if mixed else a)
+    return loops, ("A" if (mixed or inplace) else a)
 
 
 def totals_loops(n: int, names: List[str], reds: List[str], lo_names: List[str] = None) -> List[Loop]:
@@ -169,12 +190,14 @@ def dt_loop(n: int, mixed: bool = False, src: str = "A", red: str = "dtmin") -> 
     return Loop("euler_dt", (0, 0), (n, n), args + [Arg(red, REDUCE)], [GAMMA, 1.0 / n, 1.0 / n])
 
 
-def run(ex, n: int, steps: int, mixed: bool = False, U0: np.ndarray = None, totals: bool = False):
+def run(ex, n: int, steps: int, mixed: bool = False, U0: np.ndarray = None, totals: bool = False,
+        inplace: bool = False):
     """Drive `steps` time steps on an executor `ex` (decl_dat / decl_reduction /
     enqueue / reduce). Returns (time steps used, name prefix of the final state,
     per-step conserved totals if requested)."""
     U0 = initial(n) if U0 is None else U0
-    for d in datasets(n, "f32" if mixed else "f64", U0, mixed):
+    one = mixed or inplace
+    for d in datasets(n, "f32" if mixed else "f64", U0, mixed, inplace=inplace):
         ex.decl_dat(d)
     ex.decl_reduction("dtmin", "min")
     tot_names = [f"tot_{k}" for k in ("r", "mx", "my", "E")]
@@ -187,9 +210,9 @@ def run(ex, n: int, steps: int, mixed: bool = False, U0: np.ndarray = None, tota
     for _ in range(steps):
         dt = CFL * dtmin
         dts.append(dt)
-        for lp in chain_loops(n, dt, src, dst, mixed):
+        for lp in chain_loops(n, dt, src, dst, mixed, inplace=inplace):
             ex.enqueue(lp)
-        out = "A" if mixed else dst
+        out = "A" if one else dst
         if totals:
             for lp in totals_loops(n, [f"{out}_{k}" for k in ("r", "mx", "my", "E")], tot_names,
                                    [f"L_{k}" for k in ("r", "mx", "my", "E")] if mixed else None):
@@ -197,6 +220,6 @@ def run(ex, n: int, steps: int, mixed: bool = False, U0: np.ndarray = None, tota
         dtmin = ex.reduce("dtmin")
         if totals:
             tots.append([ex.reduce(t) for t in tot_names])
-        if not mixed:
+        if not one:
             src, dst = dst, src
-    return dts, ("A" if mixed else src), tots
+    return dts, ("A" if one else src), tots
