@@ -298,17 +298,16 @@ def run_variant(torch, workload, name, mixed, budget_frac, flags, planner, steps
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(streams[1])
             t0 = time.perf_counter()
-            launches = 0
             vals = None
             for _ in range(steps):
                 vals = step()
-                launches += ex.stats()["kernel_launches"]
             e1.record(streams[2])
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             dev_s = e0.elapsed_time(e1) / 1e3
             dev_s, wall = max_over_ranks(dist, [dev_s, wall], "cuda")
             s1 = ex.stats()
+            launches = s1["total_kernel_launches"] - s0["total_kernel_launches"]
             regions.append({"device_s": dev_s, "wall_s": wall, "launches": launches, "vals": vals,
                             "s0": s0, "s1": s1})
         order = sorted(range(len(regions)), key=lambda k: regions[k]["device_s"])
@@ -610,6 +609,9 @@ def main():
         "mixed_learned": (True, 1 / 3, P | C | G, oc.OC_PLAN_LEARNED),
         "fp64_plain": (False, 1 / 3, 0, oc.OC_PLAN_FIXED),
         "fp64_opt": (False, 1 / 3, P | C | G, oc.OC_PLAN_FIXED),
+        # the FP64 form with the planner's choice of tiling and residency
+        "fp64_learned": (False, 1 / 3, P | C | G, oc.OC_PLAN_LEARNED),
+        "fp64_tuned": (False, 1 / 3, P | C | G, oc.OC_PLAN_AUTOTUNE),
         "mixed_plain": (True, 1 / 3, 0, oc.OC_PLAN_FIXED),
         # the method without the learned planner: the fixed rule, every dataset streamed
         "mixed_fixed": (True, 1 / 3, P | C | G, oc.OC_PLAN_FIXED),
@@ -619,7 +621,8 @@ def main():
         "fp64_incore": (False, 1.25, G, oc.OC_PLAN_FIXED),
         "mixed_incore": (True, 1.25, G, oc.OC_PLAN_FIXED),
     }
-    planner_info = install_learned_planner(torch) if "mixed_learned" in args.variants else None
+    learned = any(variants[v][3] == oc.OC_PLAN_LEARNED for v in args.variants.split(","))
+    planner_info = install_learned_planner(torch) if learned else None
     results = {}
     clk = None
     for name in args.variants.split(","):
@@ -654,7 +657,9 @@ def main():
                 "traffic_source": tr["profile"] if tr else None,
                 "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
                 "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"],
-                "share_of_profiled_kernel_time": round(ks["ms"] / total_ms, 4)}
+                "share_of_profiled_kernel_time": round(ks["ms"] / total_ms, 4),
+                "shares": {kernel_symbol(k, head["dtype"]): round(v["ms"] / total_ms, 4)
+                           for k, v in sorted(kall.items(), key=lambda kv: -kv[1]["ms"])}}
     # binding roofline of the whole pipeline: HBM bytes at peak, link bytes at the link speed
     t_step = head["device_s"] / args.steps
     # the link rates are the better of the probes before and after the timed variants
@@ -677,6 +682,7 @@ def main():
         if r["cell_steps_per_step"]:
             variants_out[k]["cell_timesteps_per_s"] = N * r["cell_steps_per_step"] * args.steps / r["device_s"]
     for a, b in (("fp64_plain", "fp64_incore"), ("mixed_learned", "mixed_incore"), ("fp64_opt", "fp64_incore"),
+                 ("fp64_learned", "fp64_incore"), ("fp64_tuned", "fp64_incore"),
                  ("mixed_fixed", "mixed_incore"), ("mixed_um", "mixed_incore"), ("fp64_um", "fp64_incore")):
         if a in variants_out and b in variants_out:
             variants_out[a]["frac_of_incore"] = variants_out[a]["value"] / variants_out[b]["value"]

@@ -99,6 +99,11 @@ extern "C" {
  *                  graphs or autotuning trials (a trial would change the data in place); the
  *                  planner uses the fixed rule. A chain that fits the budget is one tile and
  *                  keeps its pages on the GPU. */
+/* Kernel launches: the kernels of a tile (and the reduction combine) are launched with
+ * programmatic stream serialisation (sm_90+ programmatic dependent launch): each kernel may
+ * be launched while its predecessor on the compute stream finishes, and waits for the
+ * predecessor's completion before it touches memory, so results are unchanged. The
+ * environment variable OC_PDL=0, read at oc_init, launches them plainly instead. */
 #define OC_FLAG_CYCLIC   0x1u
 #define OC_FLAG_PREFETCH 0x2u
 #define OC_FLAG_GRAPHS   0x4u
@@ -197,6 +202,7 @@ typedef struct oc_stats_t {
     int    resident_dats;  /* datasets the last flush's plan keeps resident (streamed    */
     int    pad_;           /* plans; see oc_set_residency)                              */
     double resident_bytes; /* bytes of those datasets in the device arena               */
+    double total_kernel_launches; /* kernels launched by all flushes since oc_init      */
 } oc_stats_t;
 
 /* Create the context. Sec. 4: all tiles live inside a device budget.

@@ -13,6 +13,40 @@ namespace dev {
 
 constexpr int kThreadsX = 128;
 constexpr int kRedThreads = 256;
+
+// Programmatic dependent launch (sm_90 and later). The executor launches the kernels of a
+// tile with programmatic stream serialisation, so a kernel may be launched while its
+// predecessor on the stream is still running. Every such kernel calls this first: it lets
+// its own successor launch at once (the successor's blocks are placed once all of this
+// grid's blocks have started), then waits until the predecessor grid has completed and its
+// writes are visible. Nothing is read or written before the wait, so each kernel still
+// sees every earlier kernel's results. Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch switch for the above, read once by kernels_prepare (OC_PDL=0 in the environment
+// turns the attribute off; the kernels are the same either way).
+extern bool g_pdl;
+
+// Launch of a tile kernel on `st` with programmatic stream serialisation.
+template <typename... P, typename... A>
+cudaError_t launch_tile_kernel(void (*kern)(P...), dim3 grid, int threads, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
 // points of a slow row per reduction partial (the host's kRedChunk)
 constexpr int kRedPoints = 4096;
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <type_traits>
 
@@ -73,6 +74,7 @@ __device__ __forceinline__ void lincomb_sample(const LaunchDesc& d, const T* cp,
 template <typename T, int R, int M>
 __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -119,6 +121,7 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb(const __grid_constant__ L
 template <typename T, int R, int M>
 __global__ void __launch_bounds__(kThreadsX) k_lincomb_lean(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -199,6 +202,7 @@ __device__ __forceinline__ void ring_rows(const T* base, int sl0, int r0, int S,
 template <typename T, int R, int M>
 __global__ void __launch_bounds__(kThreadsX) k_lincomb_ring(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -251,6 +255,7 @@ __global__ void __launch_bounds__(kThreadsX) k_lincomb_ring(const __grid_constan
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreadsX) k_copy_lean(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -280,6 +285,7 @@ __global__ void __launch_bounds__(kThreadsX) k_copy_lean(const __grid_constant__
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreadsX) k_copy(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -310,6 +316,7 @@ __global__ void __launch_bounds__(kThreadsX) k_copy(const __grid_constant__ Laun
 template <int R>
 __global__ void __launch_bounds__(kThreadsX) k_hilo_add(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const int x = d.lo[0] + blockIdx.x * kThreadsX + threadIdx.x;
     if (x >= d.hi[0]) return;
     const int sa = d.ndim - 1;
@@ -351,60 +358,149 @@ __device__ __forceinline__ double red_mode(double v, int mode)
     return mode == 1 ? fabs(v) : (mode == 2 ? v * v : v);
 }
 
-// Fold n consecutive elements pa[0..n) (+ pb[0..n) when pb is set) into this lane's
-// accumulator: a scalar head up to the first 16-byte boundary of pa, 16-byte vectors,
-// a scalar tail. Lane k of the warp takes head element k, vectors k, k + 32, ... and tail
-// element k (+ 32...), each in that order, so the association is fixed by the segment
-// alone. Both sources go vector only if they share their offset modulo 16.
-template <typename T>
-__device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mode, int op, double& acc)
+// Per-thread accumulators of a REDUCE (value v, mode 0: v, 1: |v|, 2: v * v).
+// FP64: every term folded in FP64.
+struct RedAccD {
+    double a;
+    __device__ __forceinline__ void init(int op) { a = red_identity(op); }
+    __device__ __forceinline__ void add(int op, int mode, double v) { a = red_apply(op, a, red_mode(v, mode)); }
+    __device__ __forceinline__ void add2(int op, int mode, double u, double v) { add(op, mode, u + v); }
+    __device__ __forceinline__ double value(int, int) const { return a; }
+};
+
+// FP32 data without FP64 arithmetic per element (GB300's FP64 rate is a small fraction
+// of its FP32 rate). A sum is kept as an unevaluated FP32 pair s + c: every term goes in
+// by Knuth's TwoSum, whose rounding error is exact and collects in c, and a square v * v
+// enters as its exact split p + e (p = fl(v * v), e = fma(v, v, -p)); the pairs are
+// folded over the warp the same way and become one FP64 value per warp. Extremes of v or |v| are exact in FP32 and a mode-2 extreme
+// is squared in FP64 at the end, which gives the FP64 fold's value. Only single-source
+// reductions and plain sums of two sources (hi + lo, added term by term) take this form.
+struct RedAccF {
+    float s, c;
+    __device__ __forceinline__ void init(int op)
+    {
+        s = op == OC_SUM ? 0.0f : (op == OC_MAX ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000));
+        c = 0.0f;
+    }
+    __device__ __forceinline__ void two_sum(float t)
+    {
+        const float u = s + t;
+        const float bp = u - s;
+        c += (s - (u - bp)) + (t - bp);
+        s = u;
+    }
+    __device__ __forceinline__ void add(int op, int mode, float v)
+    {
+        if (op == OC_SUM) {
+            if (mode == 2) {
+                const float p = v * v;
+                two_sum(p);
+                two_sum(fmaf(v, v, -p));
+            } else {
+                two_sum(mode == 1 ? fabsf(v) : v);
+            }
+        } else {
+            const float m = mode == 0 ? v : fabsf(v);
+            s = op == OC_MAX ? (m > s ? m : s) : (m < s ? m : s);
+        }
+    }
+    __device__ __forceinline__ void add2(int, int, float u, float v)
+    {
+        two_sum(u);
+        two_sum(v);
+    }
+    __device__ __forceinline__ double value(int op, int mode) const
+    {
+        if (op == OC_SUM) return (double)s + (double)c;
+        return mode == 2 && !isinf(s) ? (double)s * (double)s : (double)s;
+    }
+    // Fixed shuffle tree over the warp, still in FP32: pairs are added with TwoSum of their
+    // leading parts (the error and both trailing parts go to c); lane 0 ends with the fold.
+    __device__ __forceinline__ void warp_fold(int op)
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+            if (op == OC_SUM) {
+                const float u = s + s2;
+                const float bp = u - s;
+                c = (c + c2) + ((s - (u - bp)) + (s2 - bp));
+                s = u;
+            } else {
+                s = op == OC_MAX ? (s2 > s ? s2 : s) : (s2 < s ? s2 : s);
+            }
+        }
+    }
+};
+
+// Block fold of warp-folded FP32 accumulators (valid in lane 0 of each warp) to one FP64
+// value in thread 0: the warps' values are folded in FP64 with a fixed tree.
+__device__ __forceinline__ double block_value(const RedAccF& acc, int op, int mode)
 {
-    const int lane = (int)threadIdx.x & 31;
+    __shared__ double sm[kRedThreads / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = acc.value(op, mode);
+    __syncthreads();
+    double v = red_identity(op);
+    if (w == 0) {
+        v = l < kRedThreads / 32 ? sm[l] : red_identity(op);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v = red_apply(op, v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+// Fold n consecutive elements pa[0..n) (+ pb[0..n) when pb is set) into this thread's
+// accumulator: a scalar head up to the first 16-byte boundary of pa, 16-byte vectors,
+// a scalar tail. Thread k of the block takes head element k, vectors k, k + 256, ...
+// and tail element k (+ 256...), each in that order, so the association is fixed by the
+// segment alone. Both sources go vector only if they share their offset modulo 16.
+template <typename T, typename A>
+__device__ __forceinline__ void seg_fold(const T* pa, const T* pb, int n, int mode, int op, A& acc)
+{
     using V = typename VecOf<T>::V;
     constexpr int N = VecOf<T>::N;
     const uintptr_t ua = reinterpret_cast<uintptr_t>(pa);
     const bool vec = (ua % sizeof(T)) == 0 && (!pb || ((reinterpret_cast<uintptr_t>(pb) ^ ua) & 15) == 0);
     int head = vec ? (int)(((16 - (ua & 15)) & 15) / sizeof(T)) : n;
     if (head > n) head = n;
-    for (int i = lane; i < head; i += 32) {
-        double v = (double)__ldg(pa + i);
-        if (pb) v = v + (double)__ldg(pb + i);
-        acc = red_apply(op, acc, red_mode(v, mode));
+    for (int i = threadIdx.x; i < head; i += kRedThreads) {
+        if (pb) acc.add2(op, mode, __ldg(pa + i), __ldg(pb + i));
+        else acc.add(op, mode, __ldg(pa + i));
     }
     const int nv = (n - head) / N;
     const V* va = reinterpret_cast<const V*>(pa + head);
     const V* vb = reinterpret_cast<const V*>(pb ? pb + head : pa);
-    for (int i = lane; i < nv; i += 32) {
+    // unrolled so that a thread's independent 16-byte loads are in flight together
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nv; i += kRedThreads) {
         T ea[N], eb[N];
         *reinterpret_cast<V*>(ea) = __ldg(va + i);
         if (pb) *reinterpret_cast<V*>(eb) = __ldg(vb + i);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            double v = (double)ea[k];
-            if (pb) v = v + (double)eb[k];
-            acc = red_apply(op, acc, red_mode(v, mode));
+            if (pb) acc.add2(op, mode, ea[k], eb[k]);
+            else acc.add(op, mode, ea[k]);
         }
     }
-    for (int i = head + nv * N + lane; i < n; i += 32) {
-        double v = (double)__ldg(pa + i);
-        if (pb) v = v + (double)__ldg(pb + i);
-        acc = red_apply(op, acc, red_mode(v, mode));
+    for (int i = head + nv * N + threadIdx.x; i < n; i += kRedThreads) {
+        if (pb) acc.add2(op, mode, __ldg(pa + i), __ldg(pb + i));
+        else acc.add(op, mode, __ldg(pa + i));
     }
 }
 
-// One warp per (chunk of kRedPoints points of a slow row, slow row): blocks of
-// kRedThreads / 32 warps; warp w of block (c, g) folds chunk c of rows
-// s = lo + g * W + w, then + gridDim.y * W ... (W warps per block). The points of a row are
-// its x-lines in order (one line in 2-D, the y-lines of a z-plane in 3-D), so chunk c
+// One block per (chunk of kRedPoints points of a slow row, group of slow rows): block
+// (c, g) folds chunk c of rows s = lo + g, lo + g + gridDim.y, ... The points of a row
+// are its x-lines in order (one line in 2-D, the y-lines of a z-plane in 3-D), so chunk c
 // covers whole or partial lines; each line segment is contiguous (a REDUCE reads at
-// offset 0 inside the range, which never wraps a periodic axis). A warp has 32 lanes'
-// worth of 16-byte loads in flight per segment and folds with a fixed shuffle tree; the
-// partial of row s, chunk c is stored at part[(s - part_row0) * chunks + c], independent
-// of the tiling, so tiled and untiled runs fold the same partials in the same order.
-constexpr int kRedWarps = kRedThreads / 32;
-
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ LaunchDesc d)
+// offset 0 inside the range, which never wraps a periodic axis). Each thread folds its
+// elements into its accumulator, the block folds the threads' values with a fixed tree,
+// and the partial of row s, chunk c is stored at part[(s - part_row0) * chunks + c],
+// independent of the tiling, so tiled and untiled runs fold the same partials in the same
+// order.
+template <typename T, typename A>
+__device__ __forceinline__ void reduce_rows(const LaunchDesc& d)
 {
     const int sa = d.ndim - 1;
     const int nxr = d.hi[0] - d.lo[0];
@@ -417,32 +513,68 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ 
     const bool two = d.nargs == 3;
     const DView& a = d.v[0];
     const DView& b = d.v[1];
-    // lines touched by the chunk: one division per warp
+    // lines touched by the chunk: one division per block
     const int l0 = q1 > q0 ? (int)(q0 / nxr) : 0;
     const int l1 = q1 > q0 ? (int)((q1 - 1) / nxr) : -1;
-    const int w = (int)threadIdx.x >> 5;
-    for (int s = d.lo[sa] + (int)blockIdx.y * kRedWarps + w; s < d.hi[sa]; s += (int)gridDim.y * kRedWarps) {
+    for (int s = d.lo[sa] + (int)blockIdx.y; s < d.hi[sa]; s += (int)gridDim.y) {
         const long long ra = (long long)first_slot(a, s) * a.row_elems;
         const long long rb = two ? (long long)first_slot(b, s) * b.row_elems : 0;
-        double acc = red_identity(op);
-        for (int l = l0; l <= l1; ++l) {
-            const long long lq = (long long)l * nxr;
-            const int x0 = l == l0 ? (int)(q0 - lq) : 0;
-            const int x1 = l == l1 ? (int)(q1 - lq) : nxr;
-            const int yl = d.ndim == 3 ? d.lo[1] + l : 0;
-            const T* pa = col_ptr<T>(a, d.lo[0] + x0, yl) + ra;
-            const T* pb = two ? col_ptr<T>(b, d.lo[0] + x0, yl) + rb : nullptr;
-            seg_fold<T>(pa, pb, x1 - x0, mode, op, acc);
+        auto fold = [&](auto& acc) {
+            using Acc = typename std::remove_reference<decltype(acc)>::type;
+            acc.init(op);
+            for (int l = l0; l <= l1; ++l) {
+                const long long lq = (long long)l * nxr;
+                const int x0 = l == l0 ? (int)(q0 - lq) : 0;
+                const int x1 = l == l1 ? (int)(q1 - lq) : nxr;
+                const int yl = d.ndim == 3 ? d.lo[1] + l : 0;
+                const T* pa = col_ptr<T>(a, d.lo[0] + x0, yl) + ra;
+                const T* pb = two ? col_ptr<T>(b, d.lo[0] + x0, yl) + rb : nullptr;
+                seg_fold<T, Acc>(pa, pb, x1 - x0, mode, op, acc);
+            }
+        };
+        double v;
+        if constexpr (std::is_same<A, RedAccF>::value) {
+            RedAccF acc;
+            fold(acc);
+            acc.warp_fold(op);
+            // a sum beyond FP32's range (or an inf / NaN term) anywhere in the block: the
+            // block folds this chunk again in FP64, which gives the FP64 form's value
+            const bool out = (threadIdx.x & 31) == 0 && op == OC_SUM && !(isfinite(acc.s) && isfinite(acc.c));
+            if (__syncthreads_or(out)) {
+                RedAccD acd;
+                fold(acd);
+                v = block_fold(acd.a, op);
+            } else {
+                v = block_value(acc, op, mode);
+            }
+        } else {
+            A acc;
+            fold(acc);
+            v = block_fold(acc.a, op);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc = red_apply(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
-        if ((threadIdx.x & 31) == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = acc;
+        if (threadIdx.x == 0) d.part[(long long)(s - d.part_row0) * d.chunks + blockIdx.x] = v;
+        __syncthreads();   // the fold's shared slots are reused by the next row
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const __grid_constant__ LaunchDesc d)
+{
+    pdl_enter();
+    if constexpr (std::is_same<T, float>::value) {
+        // the FP32 form for single sources and plain two-source sums (uniform branch)
+        if (d.nargs != 3 || (d.red_op == OC_SUM && (int)d.params[0] == 0)) {
+            reduce_rows<float, RedAccF>(d);
+            return;
+        }
+    }
+    reduce_rows<T, RedAccD>(d);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_combine(const double* __restrict__ part, long long n,
                                                         int op, double* out)
 {
+    pdl_enter();
     const long long per = (n + kRedThreads - 1) / kRedThreads;
     const long long a = per * threadIdx.x;
     const long long b = a + per < n ? a + per : n;
@@ -477,8 +609,7 @@ cudaError_t launch_pointwise(const LaunchDesc& d, cudaStream_t st, F kern)
     if (nx <= 0 || ns <= 0 || (d.ndim == 3 && d.hi[1] <= d.lo[1])) return cudaSuccess;
     dim3 grid((nx + kThreadsX - 1) / kThreadsX, d.ndim == 3 ? d.hi[1] - d.lo[1] : 1,
               (ns + kRows - 1) / kRows);
-    kern<<<grid, kThreadsX, 0, st>>>(d);
-    return cudaGetLastError();
+    return launch_tile_kernel(kern, grid, kThreadsX, st, d);
 }
 
 constexpr int kLeanRows = 8;
@@ -491,8 +622,7 @@ cudaError_t launch_rows(const LaunchDesc& d, cudaStream_t st, K kern, int rows)
     const int ns = d.hi[sa] - d.lo[sa];
     if (nx <= 0 || ns <= 0 || (d.ndim == 3 && d.hi[1] <= d.lo[1])) return cudaSuccess;
     dim3 grid((nx + kThreadsX - 1) / kThreadsX, d.ndim == 3 ? d.hi[1] - d.lo[1] : 1, (ns + rows - 1) / rows);
-    kern<<<grid, kThreadsX, 0, st>>>(d);
-    return cudaGetLastError();
+    return launch_tile_kernel(kern, grid, kThreadsX, st, d);
 }
 
 // Resident blocks per SM of the ring LINCOMB instantiations ([f32][R = 4, 8][M]) and the
@@ -576,10 +706,9 @@ cudaError_t launch_loop(const LaunchDesc& d, cudaStream_t st)
         const int sa = d.ndim - 1;
         const int ns = d.hi[sa] - d.lo[sa];
         if (ns <= 0) return cudaSuccess;
-        dim3 grid(d.chunks, std::min((ns + kRedWarps - 1) / kRedWarps, 65535), 1);
-        if (f32) k_reduce<float><<<grid, kRedThreads, 0, st>>>(d);
-        else k_reduce<double><<<grid, kRedThreads, 0, st>>>(d);
-        return cudaGetLastError();
+        dim3 grid(d.chunks, std::min(ns, 65535), 1);
+        return f32 ? launch_tile_kernel(k_reduce<float>, grid, kRedThreads, st, d)
+                   : launch_tile_kernel(k_reduce<double>, grid, kRedThreads, st, d);
     }
     default:
         return launch_physics(d, st);
@@ -598,15 +727,20 @@ cudaError_t launch_strips(const StripBatch& b, cudaStream_t st)
 
 cudaError_t launch_combine(const double* part, long long n, int op, double* out, cudaStream_t st)
 {
-    k_combine<<<1, kRedThreads, 0, st>>>(part, n, op, out);
-    return cudaGetLastError();
+    return launch_tile_kernel(k_combine, dim3(1, 1, 1), kRedThreads, st, part, n, op, out);
 }
 
 int kernels_compiled_arch() { return 1030; }
 
+namespace dev {
+bool g_pdl = true;
+}
+
 void kernels_prepare()
 {
     if (g_sms > 0) return;
+    const char* pdl = getenv("OC_PDL");
+    dev::g_pdl = !(pdl && pdl[0] == '0');
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();

@@ -108,6 +108,7 @@ __device__ __forceinline__ T Lk(const LaunchDesc& d, int arg, const Pt& p, const
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_prim(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T gamma = params_of<T>(d)[0];
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_prim(const __grid_constant_
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_flux(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T mx = L<T, O>(d, 1, p), my = L<T, O>(d, 2, p), E = L<T, O>(d, 3, p);
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_flux(const __grid_constant_
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_pred(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T lx = params_of<T>(d)[0], ly = params_of<T>(d)[1];
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_pred(const __grid_constant_
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_euler_corr(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T* pm = params_of<T>(d);
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(kThreadsX) k_euler_corr(const __grid_constant_
 template <typename T, bool O>
 __global__ void __launch_bounds__(kRedThreads) k_euler_dt(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     const T* pm = params_of<T>(d);
     const T gamma = pm[0], dx = pm[1], dy = pm[2];
     const bool lo = d.nargs == 9;
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(kRedThreads) k_euler_dt(const __grid_constant_
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_prim(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T gamma = params_of<T>(d)[0], Ma = params_of<T>(d)[1];
@@ -230,6 +236,7 @@ __device__ __forceinline__ T d1(const LaunchDesc& d, int arg, const Pt& p, const
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_grad(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T* pm = params_of<T>(d);
@@ -275,6 +282,7 @@ __device__ __forceinline__ void ns_fluxes(const T (&in)[21], int a, T mu, T kc, 
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_rhs(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T* pd = params_of<T>(d);
@@ -310,6 +318,7 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_rhs(const __grid_constant__ La
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_flux(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T* pd = params_of<T>(d);
@@ -331,6 +340,7 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_flux(const __grid_constant__ L
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T* pd = params_of<T>(d);
@@ -355,6 +365,7 @@ __global__ void __launch_bounds__(kThreadsX) k_ns_div(const __grid_constant__ La
 template <typename T, bool O>
 __global__ void __launch_bounds__(kThreadsX) k_ns_update(const __grid_constant__ LaunchDesc d)
 {
+    pdl_enter();
     Pt p;
     if (!point_of(d, p)) return;
     const T B = params_of<T>(d)[0];
@@ -370,8 +381,7 @@ cudaError_t launch_pt(const LaunchDesc& d, cudaStream_t st, K kern)
     const int ny = d.ndim == 3 ? d.hi[1] - d.lo[1] : 1;
     if (nx <= 0 || ns <= 0 || ny <= 0) return cudaSuccess;
     dim3 grid((nx + kThreadsX - 1) / kThreadsX, ny, ns);
-    kern<<<grid, kThreadsX, 0, st>>>(d);
-    return cudaGetLastError();
+    return launch_tile_kernel(kern, grid, kThreadsX, st, d);
 }
 
 }  // namespace
@@ -392,13 +402,12 @@ cudaError_t launch_physics(const LaunchDesc& d, cudaStream_t st)
         if (ns <= 0) return cudaSuccess;
         dim3 grid(d.chunks, ns, 1);
         if (f) {
-            if (o) k_euler_dt<float, true><<<grid, kRedThreads, 0, st>>>(d);
-            else k_euler_dt<float, false><<<grid, kRedThreads, 0, st>>>(d);
+            return o ? launch_tile_kernel(k_euler_dt<float, true>, grid, kRedThreads, st, d)
+                     : launch_tile_kernel(k_euler_dt<float, false>, grid, kRedThreads, st, d);
         } else {
-            if (o) k_euler_dt<double, true><<<grid, kRedThreads, 0, st>>>(d);
-            else k_euler_dt<double, false><<<grid, kRedThreads, 0, st>>>(d);
+            return o ? launch_tile_kernel(k_euler_dt<double, true>, grid, kRedThreads, st, d)
+                     : launch_tile_kernel(k_euler_dt<double, false>, grid, kRedThreads, st, d);
         }
-        return cudaGetLastError();
     }
     case OC_K_NS_PRIM: return OC_PT(k_ns_prim);
     case OC_K_NS_GRAD: return OC_PT(k_ns_grad);

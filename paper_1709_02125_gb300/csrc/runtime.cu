@@ -1590,6 +1590,7 @@ static int finish_chain(Plan& P, const std::vector<Loop>& loops, bool trial, boo
     S.total_hbm_bytes += S.hbm_bytes;
     S.total_h2d_bytes += S.h2d_bytes;
     S.total_d2h_bytes += S.d2h_bytes;
+    S.total_kernel_launches += S.kernel_launches;
     S.chains++;
     return OC_OK;
 }

@@ -54,7 +54,8 @@ class OcStats(ctypes.Structure):
                 ("total_seconds", ctypes.c_double), ("total_cell_updates", ctypes.c_double),
                 ("total_hbm_bytes", ctypes.c_double), ("total_h2d_bytes", ctypes.c_double),
                 ("total_d2h_bytes", ctypes.c_double), ("chains", ctypes.c_longlong),
-                ("resident_dats", ctypes.c_int), ("pad_", ctypes.c_int), ("resident_bytes", ctypes.c_double)]
+                ("resident_dats", ctypes.c_int), ("pad_", ctypes.c_int), ("resident_bytes", ctypes.c_double),
+                ("total_kernel_launches", ctypes.c_double)]
 
 
 class OcKernelStats(ctypes.Structure):
