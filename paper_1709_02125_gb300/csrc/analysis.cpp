@@ -409,9 +409,12 @@ int fit_tile_height(const std::vector<Loop>& loops, const std::vector<Dat>& dats
         int mid = lo + (hi - lo) / 2;
         if (fits(mid)) lo = mid; else hi = mid;
     }
-    // the same number of tiles, evened out: no short last tile (a phase of its own)
+    // the same number of tiles, evened out: no short last tile (a phase of its own). A
+    // plan's size is not monotonic in h (slab rows follow where the skewed tile
+    // boundaries fall), so the evened height is used only if its plan fits too.
     const int T = (span + lo - 1) / lo;
-    return (span + T - 1) / T;
+    const int even = (span + T - 1) / T;
+    return even == lo || fits(even) ? even : lo;
 }
 
 Residency choose_residency(const std::vector<Loop>& loops, const std::vector<Dat>& dats,

@@ -353,3 +353,20 @@ def test_residency_plan_layout(lib):
         with pytest.raises(oc.OcError) as e:
             ex.set_residency(1.0)
         assert e.value.code == oc.OC_ERR_ARG
+
+
+@pytest.mark.parametrize("seed", [9, 14, 25, 56])
+def test_planner_height_always_fits(lib, seed):
+    """The planner's tile height (bisection for the largest fitting height, then evened
+    out over the same number of tiles) gives a plan inside the budget even where plan
+    size is not monotonic in the height: on these chains (depth 2, cyclic + prefetch,
+    half the footprint) the evened height alone needed up to 1.6x the budget."""
+    rng = np.random.default_rng(seed)
+    nd = int(rng.integers(2, 4))
+    n = int(rng.choice([48, 64, 96]))
+    nf, nl, rad = int(rng.integers(6, 16)), int(rng.integers(8, 40)), int(rng.integers(1, 3))
+    dats, reds, loops = random_chain.build_general(nd, n, nf, nl, rad, seed, nz=n)
+    fp = sum(int(np.prod(d.shape)) * 8 for d in dats)
+    plan, st, _ = dry(fp // 2, dats, reds, loops, h=0, depth=2, flags=oc.OC_FLAG_CYCLIC | oc.OC_FLAG_PREFETCH)
+    assert plan["tiles"] > 1 and st["tiles"] == plan["tiles"]
+    plan_sim.check_legality(plan, loops)
