@@ -738,9 +738,9 @@ bool g_pdl = true;
 
 void kernels_prepare()
 {
-    if (g_sms > 0) return;
     const char* pdl = getenv("OC_PDL");
     dev::g_pdl = !(pdl && pdl[0] == '0');
+    if (g_sms > 0) return;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
