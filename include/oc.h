@@ -156,9 +156,15 @@ extern "C" {
  *               b = x_{1 mod M}, c = x_{2 mod M}. dst(p) = acc. FP32 datasets use
  *               the parameters rounded to float.
  * OC_K_REDUCE   args: [0] READ src0 (offset 0), optionally [1] READ src1 (offset 0),
- *               last: REDUCE handle. v = src0(p) (+ src1(p)), converted to double
- *               before the addition; params = [mode]: 0 -> v, 1 -> |v|, 2 -> v*v.
- *               The handle's operator folds v over the range (see oc_reduce).
+ *               last: REDUCE handle. v = src0(p) (+ src1(p)); params = [mode]:
+ *               0 -> v, 1 -> |v|, 2 -> v*v. The handle's operator folds v over the
+ *               range into one FP64 partial per slow row and 4096-point chunk, in a
+ *               fixed order (see oc_reduce). FP64 data fold in FP64. FP32 data fold
+ *               without FP64 arithmetic per point: a sum is a compensated FP32 pair per
+ *               thread and warp (TwoSum; a square enters as its exact FMA split),
+ *               within ~1e-13 of sum |terms| of the exact sum; extremes are exact; a
+ *               two-source |v|, square or extreme folds in FP64 (hi + lo exact there);
+ *               a block whose FP32 sum overflows folds again in FP64.
  * OC_K_HILO_ADD args: [0] RW hi (F32), [1] RW lo (F32), [2] READ du (offset 0).
  *               params = [scale]. Compensated update of the pair value hi+lo by
  *               y = (float)scale * du, all in FP32: s = hi + y; z = s - hi;
