@@ -60,8 +60,3 @@ def ns_step(U: np.ndarray, dt: float, prm: np.ndarray):
     _, nz, ny, nx = U.shape
     _L().or_ns_step(nx, ny, nz, _c(U), dt, _c(prm))
     return U
-
-
-def run_loop(loop, fields, reds, red_ops):
-    raise NotImplementedError(
-        "the oracle evaluates PDE workloads through euler_step / ns_step, not loop by loop")
